@@ -1,0 +1,260 @@
+"""Pins for the CPU oracle: closed forms, brute force, exact Pauli closure,
+invariants, and planted mistakes that each pin must catch.  No GPU."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle.closure as oc
+from paper_2506_01120_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _dim(labels=None, gens=None, tol=1e-10, **kw):
+    if gens is None:
+        gens = inputs.generators_from_labels(labels)
+    return oc.alg4_orthonormalization(gens, tol, **kw)
+
+
+# ------------------------------------------------------------ primitives
+def _sl2():
+    E = np.array([[0, 1], [0, 0]], dtype=np.complex128)
+    F = np.array([[0, 0], [1, 0]], dtype=np.complex128)
+    H = np.array([[1, 0], [0, -1]], dtype=np.complex128)
+    return E, F, H
+
+
+def test_sl2_relations():
+    """Textbook sl(2) relations: [E, F] = H, [H, E] = 2E, [H, F] = -2F."""
+    E, F, H = _sl2()
+    np.testing.assert_array_equal(oc.bracket(E, F), H)
+    np.testing.assert_array_equal(oc.bracket(H, E), 2 * E)
+    np.testing.assert_array_equal(oc.bracket(H, F), -2 * F)
+
+
+def test_pauli_algebra_closed_forms():
+    """[iX, iY] = -[X, Y] = -2iZ; <iP, iQ> = delta_PQ for Pauli strings."""
+    X, Y, Z = (inputs.pauli_matrix(c) for c in "XYZ")
+    np.testing.assert_allclose(oc.bracket(1j * X, 1j * Y), -2j * Z, atol=0)
+    np.testing.assert_allclose(oc.bracket(1j * Y, 1j * X), 2j * Z, atol=0)
+    assert oc.inner(1j * Y, 1j * Y) == pytest.approx(1.0)
+    assert abs(oc.inner(1j * X, 1j * Y)) == 0.0
+    assert oc.norm(2j * Z) == pytest.approx(2.0)
+    # <a, b> is conjugate-linear in a: <i a, b> = -i <a, b>
+    a = inputs.random_antihermitian(4, np.random.default_rng(0))
+    b = inputs.random_antihermitian(4, np.random.default_rng(1))
+    assert oc.inner(1j * a, b) == pytest.approx(-1j * oc.inner(a, b))
+    # anti-Hermitian operands give a real inner product
+    assert abs(oc.inner(a, b).imag) < 1e-15
+
+
+def test_project_out_matches_least_squares():
+    """h - proj_V h equals the least-squares residual against span(V)."""
+    rng = np.random.default_rng(3)
+    d = 4
+    V = oc.alg4_orthonormalization(np.stack([inputs.random_antihermitian(d, rng) for _ in range(5)]),
+                                   1e-10, max_candidates=0).basis
+    h = inputs.random_antihermitian(d, rng)
+    r = oc.project_out(V, h)
+    A = V.reshape(V.shape[0], -1).T
+    coef, *_ = np.linalg.lstsq(A, h.reshape(-1), rcond=None)
+    np.testing.assert_allclose(r.reshape(-1), h.reshape(-1) - A @ coef, atol=1e-13)
+
+
+# ------------------------------------------------------------ closed forms
+@pytest.mark.parametrize("n", [2, 3, 4])
+def test_so2n_chain(n):
+    """Open chain {iX_j, iZ_jZ_{j+1}} maps (Jordan-Wigner) to nearest-neighbour
+    Majorana bilinears, which generate so(2n): dimension n(2n-1)."""
+    res = _dim(inputs.so2n_chain_labels(n))
+    assert res.dim == n * (2 * n - 1)
+
+
+def test_su2n_chain_matches_paper_table():
+    """{iX_j, iY_j, iZ_jZ_{j+1}} is controllable: dimension 4^n - 1, the value
+    Table 1(a) prints for each n."""
+    table = json.load(open(os.path.join(GOLDEN, "paper_dims.json")))["table1a_hea"]
+    printed = dict(zip(table["n"], table["dim"]))
+    for n in (2, 3):
+        res = _dim(inputs.su2n_chain_labels(n))
+        assert res.dim == printed[n] == 4 ** n - 1
+    res = _dim(inputs.su2n_chain_labels(4), saturation_exit=True)
+    assert res.dim == printed[4] == 255 and res.saturated
+
+
+def test_table2_basis_matrix_size():
+    """Table 2 prints the d^2 x |B| basis-matrix size for dims 4095 and 16383."""
+    t = json.load(open(os.path.join(GOLDEN, "paper_dims.json")))["table2_hea_sparse"]
+    for n, dim, size in zip(t["n"], t["dim"], t["basis_matrix_size"]):
+        assert dim == 4 ** n - 1
+        assert abs(4 ** n * dim - size) / size < 0.01
+
+
+@pytest.mark.parametrize("d", [2, 3, 4, 6])
+def test_random_pair_generates_su_or_u(d):
+    """A generic traceless pair generates su(d) (d^2 - 1); keeping the trace adds
+    the centre direction and gives u(d) (d^2)."""
+    rng = np.random.default_rng(10 + d)
+    g = np.stack([inputs.random_antihermitian(d, rng) for _ in range(2)])
+    assert _dim(gens=g, tol=1e-8).dim == d * d - 1
+    g2 = np.stack([inputs.random_antihermitian(d, rng, traceless=False) for _ in range(2)])
+    assert _dim(gens=g2, tol=1e-8).dim == d * d
+
+
+def test_degenerate_sets():
+    """Commuting sets give dim k; one generator gives 1; repeats and multiples are
+    rejected in the generator pass; the zero operator is never accepted."""
+    lab = ["ZII", "IZI", "ZZI", "IIZ"]
+    assert _dim(lab).dim == 4
+    assert _dim(["XYZ"]).dim == 1
+    g = inputs.generators_from_labels(["XI", "XI", "IZ"])
+    g[1] *= 3.0
+    assert _dim(gens=g).dim == 2
+    z = np.zeros((2, 4, 4), dtype=np.complex128)
+    assert _dim(gens=z).dim == 0
+    # a dependent combination of earlier generators is rejected
+    a, b = inputs.generators_from_labels(["XX", "ZZ"])
+    assert _dim(gens=np.stack([a, b, 0.3 * a - 2 * b])).dim == 2
+
+
+# ------------------------------------------------------ brute force (Alg. 1)
+@pytest.mark.parametrize("seed", range(12))
+def test_alg4_equals_alg1_rank(seed):
+    """Algorithm 4 and Algorithm 1 with an SVD rank test give the same dimension
+    (Section 3.2: the two methods yield the same algebra)."""
+    rng = np.random.default_rng(seed)
+    d = int(rng.choice([2, 4, 8]))
+    n = int(np.log2(d))
+    if seed % 2 == 0:
+        labels = inputs.random_pauli_labels(n, int(rng.integers(1, 4)), rng, max_weight=min(3, n))
+        g = inputs.generators_from_labels(labels)
+    else:
+        d = int(rng.choice([2, 3, 4]))
+        k = int(rng.integers(1, 3))
+        g = np.stack([inputs.random_antihermitian(d, rng) for _ in range(k)])
+    r4 = oc.alg4_orthonormalization(g, 1e-10)
+    b1 = oc.alg1_rank(g)
+    assert r4.dim == b1.shape[0]
+    # same span: B from Alg. 1 is not orthonormal, compare spans
+    if r4.dim:
+        assert oc.span_distance(r4.basis, b1) < 1e-9
+
+
+# ------------------------------------------------------- exact Pauli closure
+def test_pauli_closure_closed_forms():
+    assert len(oc.pauli_closure(inputs.so2n_chain_labels(3))) == 15
+    assert len(oc.pauli_closure(inputs.so2n_chain_labels(10))) == 190
+    assert len(oc.pauli_closure(inputs.su2n_chain_labels(6))) == 4095
+    assert len(oc.pauli_closure(["X", "Z"])) == 3
+    assert len(oc.pauli_closure(["ZI", "IZ"])) == 2
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_alg4_equals_pauli_closure(seed):
+    """For Pauli-string generators the closure is spanned by the strings reached by
+    the bracket, so Algorithm 4 and the exact integer closure agree, string by
+    string (each accepted V element is +-i times one string)."""
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.choice([2, 3, 4]))
+    labels = inputs.random_pauli_labels(n, int(rng.integers(2, 6)), rng, max_weight=min(3, n))
+    strings = oc.pauli_closure(labels)
+    res = oc.alg4_orthonormalization(inputs.generators_from_labels(labels), 1e-10)
+    assert res.dim == len(strings)
+    U = inputs.generators_from_labels(strings)
+    assert oc.span_distance(res.basis, U) < 1e-12
+
+
+# ------------------------------------------------------------- invariants
+@pytest.mark.parametrize("case", ["so6", "random3"])
+def test_basis_invariants(case):
+    if case == "so6":
+        g = inputs.generators_from_labels(inputs.so2n_chain_labels(3))
+        tol = 1e-10
+    else:
+        g = inputs.random_set(3, 2, seed=7)
+        tol = 1e-8
+    res = oc.alg4_orthonormalization(g, tol)
+    V = res.basis
+    assert oc.ortho_defect(V) < 1e-12
+    assert oc.closure_residual(V) < 10 * tol
+    for v in V:
+        np.testing.assert_allclose(v, -v.conj().T, atol=1e-14)        # anti-Hermitian
+    for i in range(len(V)):
+        for j in range(i):
+            assert abs(np.trace(oc.bracket(V[i], V[j]))) < 1e-13      # traceless brackets
+    assert res.max_imag_beta < 1e-14
+
+
+def test_span_distance_known_angle():
+    """sin of a rotation angle out of the span is recovered exactly."""
+    labels = ["XI", "ZI", "IX", "IZ"]
+    V = inputs.generators_from_labels(labels)
+    W = inputs.generators_from_labels(["YY"])[0]
+    for theta in (1e-9, 1e-3, 0.7):
+        U = V.copy()
+        U[2] = np.cos(theta) * V[2] + np.sin(theta) * W
+        assert oc.span_distance(V, U) == pytest.approx(np.sin(theta), rel=1e-6, abs=1e-15)
+    assert oc.span_distance(V, V[[1, 0, 3, 2]]) < 1e-15
+    assert oc.span_distance(V, V[:3]) == 1.0
+
+
+def test_resume_matches_single_run():
+    """The (V, l, m) cursor state is complete: a run split in two equals one run."""
+    g = inputs.generators_from_labels(inputs.su2n_chain_labels(2))
+    full = oc.alg4_orthonormalization(g, 1e-10)
+    part = oc.alg4_orthonormalization(g, 1e-10, max_candidates=17)
+    part = oc.alg4_orthonormalization(g, 1e-10, resume=part)
+    assert part.dim == full.dim
+    np.testing.assert_allclose(part.basis, full.basis, atol=1e-14)
+
+
+# ------------------------------------------------------- planted mistakes
+def _pins_pass():
+    """A compact subset of the pins above; True iff all hold."""
+    try:
+        if _dim(inputs.so2n_chain_labels(3)).dim != 15:
+            return False
+        if _dim(inputs.su2n_chain_labels(2)).dim != 15:
+            return False
+        g = inputs.random_set(3, 2, seed=7)
+        res = oc.alg4_orthonormalization(g, 1e-8)
+        if res.dim != 8 or oc.ortho_defect(res.basis) > 1e-12:
+            return False
+        if oc.closure_residual(res.basis) > 1e-7:
+            return False
+        X, Y, Z = (inputs.pauli_matrix(c) for c in "XYZ")
+        if not np.allclose(oc.bracket(1j * X, 1j * Y), -2j * Z):
+            return False
+        E, F, H = _sl2()
+        if not (np.allclose(oc.bracket(E, F), H) and np.allclose(oc.bracket(H, E), 2 * E)):
+            return False
+        return True
+    except Exception:
+        return False
+
+
+def test_pins_pass_unpatched():
+    assert _pins_pass()
+
+
+@pytest.mark.parametrize("mistake", ["anticommutator", "no_conjugate", "transposed_operand",
+                                     "dropped_projection_term", "wrong_inner_scale"])
+def test_planted_mistake_is_caught(monkeypatch, mistake):
+    """Each plausible slip in the oracle's arithmetic makes a pin fail."""
+    if mistake == "anticommutator":
+        monkeypatch.setattr(oc, "bracket", lambda a, b: a @ b + b @ a)
+    elif mistake == "no_conjugate":
+        monkeypatch.setattr(oc, "coefficients",
+                            lambda V, h: np.einsum("ljk,jk->l", V, h) / h.shape[0])
+        monkeypatch.setattr(oc, "inner", lambda a, b: np.trace(a.T @ b) / a.shape[0])
+    elif mistake == "transposed_operand":
+        monkeypatch.setattr(oc, "bracket", lambda a, b: a.T @ b - b @ a.T)
+    elif mistake == "dropped_projection_term":
+        orig = oc.project_out
+        monkeypatch.setattr(oc, "project_out", lambda V, h: orig(V[:-1], h) if len(V) > 1 else orig(V, h))
+    elif mistake == "wrong_inner_scale":
+        monkeypatch.setattr(oc, "coefficients",
+                            lambda V, h: np.einsum("ljk,jk->l", V.conj(), h))
+    assert not _pins_pass()
