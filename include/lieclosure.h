@@ -1,0 +1,181 @@
+/*
+ * lieclosure.h -- C ABI of the GB300 (sm_103a) Lie-closure library.
+ *
+ * The library computes the closure of a set of d x d anti-Hermitian matrices
+ * with Algorithm 4 of Iiyama, "Fast numerical generation of Lie closure"
+ * (arXiv 2506.01120, Section 3.2): a generator pass, then a sweep over brackets
+ * [V[l], V[m]] of the growing orthonormal basis V, each tested for linear
+ * independence by projecting it onto span(V) (the Corollary of Theorem 1) and
+ * appended, normalised, when its orthogonal part is non-zero.
+ *
+ * Definitions used throughout (Section 2.2 of the paper):
+ *   bracket        [a, b] = ab - ba
+ *   inner product  <a, b> = tr(a^dagger b) / d
+ *   norm           ||a|| = sqrt(<a, a>)
+ * Every basis element written by the library has ||v|| = 1 in this norm, i.e.
+ * Frobenius norm sqrt(d), and <v_i, v_j> = delta_ij.
+ *
+ * Independence test ("h_perp != 0" in Algorithm 4, which the paper leaves
+ * without a tolerance): a candidate h is accepted iff ||h|| > eta_abs and
+ * ||h - proj_V h|| > tol * ||h||, the residual taken from two classical
+ * Gram-Schmidt passes in FP64.  Each bracket (l, m), m < l, is formed once, in
+ * the order l = 1, 2, ..., m = 0 .. l-1, and the sweep ends when l reaches |V|.
+ *
+ * Memory and threading: the library allocates its own device workspace for
+ * the duration of a call (through a stream-ordered pool it keeps per device)
+ * and frees it before returning; nothing it allocates is handed to the caller.
+ * Calls on different streams may run concurrently; one call per stream.
+ * No call uses more than the current CUDA device.
+ */
+#ifndef LIECLOSURE_H
+#define LIECLOSURE_H
+
+#if defined(__GNUC__)
+#define LC_API __attribute__((visibility("default")))
+#else
+#define LC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Interleaved complex128, the layout of numpy.complex128 and std::complex<double>. */
+typedef struct { double re, im; } lc_c128;
+
+typedef enum {
+  LC_OK = 0,
+  LC_ERR_ARG = -1,               /* null pointer, k < 1, d < 1, tol <= 0, bad option */
+  LC_ERR_NOT_ANTIHERMITIAN = -2, /* some generator has |g + g^dagger| > 1e-12 max|g| */
+  LC_ERR_NONFINITE = -3,         /* NaN or Inf in the generators */
+  LC_ERR_CAPACITY = -4,          /* the basis would exceed max_dim; dim_out = max_dim */
+  LC_ERR_CUDA = -5,              /* a CUDA runtime call failed */
+  LC_ERR_OOM = -6,               /* device workspace could not be allocated */
+  LC_ERR_TIMEOUT = -7            /* a bounded device-side wait ran out */
+} lc_status;
+
+typedef enum {
+  /* every product, projection and residual in FP64 (SIMT) */
+  LC_PREC_FP64 = 0,
+  /* brackets and projections screened with split-BF16 tensor-core products
+     (three BF16 MMAs per product, FP32 accumulation); candidates whose
+     screened relative residual exceeds tau_screen are recomputed and decided
+     in FP64, so every accepted element is an FP64 result */
+  LC_PREC_MIXED_BF16X3 = 1
+} lc_precision;
+
+typedef struct {
+  int precision;              /* lc_precision; default LC_PREC_MIXED_BF16X3 */
+  double eta_abs;             /* absolute floor on ||h||; default 1e-12 */
+  double tau_screen;          /* mixed mode: relative residual below which a
+                                 screened candidate is rejected without the FP64
+                                 recheck; 0 = default (1e-3) */
+  int block_k;                /* candidates per block; 0 = automatic */
+  int saturation_exit;        /* nonzero: stop once |V| reaches the largest
+                                 possible dimension (d^2 - 1, plus one if a
+                                 generator has a trace); not in the paper,
+                                 default 0 */
+  long long spin_cap;         /* iteration bound for device spin-waits; 0 = default */
+  long long max_candidates;   /* stop after this many bracket candidates
+                                 (0 = run to the end); the report then carries
+                                 the cursor (l, m) */
+  int verbose;                /* nonzero: per-block log lines on stderr */
+  int profile;                /* nonzero: time each phase with CUDA events on
+                                 the call's stream (lc_report.t_phase_s) */
+} lc_options;
+
+typedef struct {
+  long long dim;              /* |V| on return */
+  long long brackets_checked; /* bracket candidates tested */
+  long long generators_checked;
+  long long n_nonzero;        /* bracket candidates with ||h|| above the floor */
+  long long n_flagged;        /* candidates sent to the FP64 accept step */
+  long long n_blocks;
+  long long cursor_l, cursor_m; /* next pair of the sweep on return */
+  double t_total_s;           /* wall time of the call */
+  double t_last_accept_s;     /* wall time at the last accepted element */
+  double min_acc_rel_res;     /* smallest relative residual among accepts */
+  double max_rej_rel_res;     /* largest FP64 relative residual among flagged rejects */
+  double tau_screen;          /* screen threshold used (mixed mode) */
+  double max_screen_rej_rel_res; /* largest screened relative residual among
+                                 candidates the screen rejected (after the
+                                 basis stops growing this is the noise floor
+                                 of the screen) */
+  long long kernel_launches;  /* kernels this call launched */
+  long long gemm_launches;    /* screening GEMM launches (projection + residual) */
+  double gemm_flops;          /* sum over those launches of 3 * 2 * rows * cols *
+                                 depth with the unpadded extents (three split
+                                 products per multiply-add) */
+  double t_phase_s[6];        /* with opt.profile: device time per phase --
+                                 0 brackets, 1 projection GEMM, 2 residual GEMM,
+                                 3 screen, 4 FP64 accept, 5 other */
+  int precision;
+  int status;
+} lc_report;
+
+/* Fills *opt with the defaults listed above. */
+LC_API void lc_default_options(lc_options* opt);
+
+/* Static, human-readable name of a status code. */
+LC_API const char* lc_status_string(int status);
+
+/* Library version string. */
+LC_API const char* lc_version(void);
+
+/*
+ * lie_closure -- Algorithm 4 on one generator set (Section 3.2), host buffers.
+ *
+ * generators : k x d x d complex128, row-major, host memory, caller-owned,
+ *              read only.  Each must be anti-Hermitian (g^dagger = -g) within
+ *              1e-12 * max|g|; they are taken in the given order.
+ * k, d       : number of generators (>= 1) and matrix size (>= 2).
+ * tol        : relative residual tolerance (> 0) of the independence test.
+ * basis_out  : host buffer for max_dim x d x d complex128 (row-major), or NULL
+ *              to return the dimension only.  On LC_OK and LC_ERR_CAPACITY the
+ *              first *dim_out elements are the orthonormal basis V in the
+ *              order Algorithm 4 appends them.
+ * dim_out    : receives |V| (always written when non-NULL).
+ * max_dim    : capacity of basis_out in elements (>= 1); the library also uses
+ *              it to size its device basis.  d*d always suffices.
+ * opt, rep   : options (NULL = defaults) and report (NULL = none).
+ * Returns an lc_status.  On error the contents of basis_out are unspecified
+ * beyond *dim_out elements.
+ */
+LC_API int lie_closure(const lc_c128* generators, int k, int d, double tol,
+                lc_c128* basis_out, long long* dim_out, long long max_dim,
+                const lc_options* opt, lc_report* rep);
+
+/*
+ * lie_closure_dev -- as lie_closure, with device buffers and a stream.
+ *
+ * generators and basis_out are device pointers of the current device
+ * (basis_out may be NULL); stream is a cudaStream_t passed as void*
+ * (NULL = the legacy default stream).  The call is synchronous with respect
+ * to the host: it returns after the stream has finished its work.
+ */
+LC_API int lie_closure_dev(const lc_c128* generators, int k, int d, double tol,
+                    lc_c128* basis_out, long long* dim_out, long long max_dim,
+                    const lc_options* opt, lc_report* rep, void* stream);
+
+/*
+ * lie_closure_batched -- Algorithm 4 on nsets independent generator sets
+ * (Section 3.2 applied per set), host buffers.
+ *
+ * generators[s] : k[s] x d[s] x d[s] complex128 host array of set s.
+ * basis_out[s]  : host buffer of max_dim[s] x d[s] x d[s] complex128 or NULL;
+ *                 basis_out itself may be NULL (dimensions only).
+ * max_dim[s]    : capacity of set s (>= 1).
+ * dim_out[s], status_out[s] : per-set dimension and lc_status.
+ * rep           : NULL or an array of nsets reports.
+ * Returns LC_OK if every set returned LC_OK, else the first failing status.
+ */
+LC_API int lie_closure_batched(int nsets, const lc_c128* const* generators, const int* k,
+                        const int* d, double tol, lc_c128* const* basis_out,
+                        const long long* max_dim, long long* dim_out, int* status_out,
+                        const lc_options* opt, lc_report* rep);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIECLOSURE_H */

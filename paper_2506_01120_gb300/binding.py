@@ -1,0 +1,224 @@
+"""ctypes binding of ``liblieclosure.so`` (argument marshalling only).
+
+Every function here forwards to the C ABI of ``include/lieclosure.h`` /
+``include/lieclosure_kernels.h`` under the same name; all computation runs in
+the library's CUDA kernels.  The library is loaded on first use; if it is
+missing (not built) the call raises ``LibraryNotBuilt`` -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblieclosure.so")
+
+LC_OK = 0
+LC_ERR_ARG = -1
+LC_ERR_NOT_ANTIHERMITIAN = -2
+LC_ERR_NONFINITE = -3
+LC_ERR_CAPACITY = -4
+LC_ERR_CUDA = -5
+LC_ERR_OOM = -6
+LC_ERR_TIMEOUT = -7
+
+LC_PREC_FP64 = 0
+LC_PREC_MIXED_BF16X3 = 1
+PRECISIONS = {"fp64": LC_PREC_FP64, "mixed": LC_PREC_MIXED_BF16X3}
+
+# every symbol the public headers declare
+EXPORTED = ["lc_default_options", "lc_status_string", "lc_version", "lie_closure", "lie_closure_dev",
+            "lie_closure_batched", "lc_split_gemm_f32"]
+
+
+class LibraryNotBuilt(RuntimeError):
+    pass
+
+
+class LieClosureError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lie_closure failed: {msg} (status {status})")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("eta_abs", ctypes.c_double), ("tau_screen", ctypes.c_double),
+                ("block_k", ctypes.c_int), ("saturation_exit", ctypes.c_int), ("spin_cap", ctypes.c_longlong),
+                ("max_candidates", ctypes.c_longlong), ("verbose", ctypes.c_int), ("profile", ctypes.c_int)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_longlong), ("brackets_checked", ctypes.c_longlong),
+                ("generators_checked", ctypes.c_longlong), ("n_nonzero", ctypes.c_longlong),
+                ("n_flagged", ctypes.c_longlong), ("n_blocks", ctypes.c_longlong),
+                ("cursor_l", ctypes.c_longlong), ("cursor_m", ctypes.c_longlong),
+                ("t_total_s", ctypes.c_double), ("t_last_accept_s", ctypes.c_double),
+                ("min_acc_rel_res", ctypes.c_double), ("max_rej_rel_res", ctypes.c_double),
+                ("tau_screen", ctypes.c_double), ("max_screen_rej_rel_res", ctypes.c_double),
+                ("kernel_launches", ctypes.c_longlong), ("gemm_launches", ctypes.c_longlong),
+                ("gemm_flops", ctypes.c_double), ("t_phase_s", ctypes.c_double * 6),
+                ("precision", ctypes.c_int), ("status", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if name == "t_phase_s" else v
+        return out
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises LibraryNotBuilt when it is absent)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise LibraryNotBuilt(f"{LIB_PATH} is missing: run paper_2506_01120_gb300.build.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        c_p = ctypes.c_void_p
+        L.lc_default_options.argtypes = [ctypes.POINTER(Options)]
+        L.lc_default_options.restype = None
+        L.lc_status_string.argtypes = [ctypes.c_int]
+        L.lc_status_string.restype = ctypes.c_char_p
+        L.lc_version.argtypes = []
+        L.lc_version.restype = ctypes.c_char_p
+        L.lie_closure.argtypes = [c_p, ctypes.c_int, ctypes.c_int, ctypes.c_double, c_p,
+                                  ctypes.POINTER(ctypes.c_longlong), ctypes.c_longlong,
+                                  ctypes.POINTER(Options), ctypes.POINTER(Report)]
+        L.lie_closure.restype = ctypes.c_int
+        L.lie_closure_dev.argtypes = L.lie_closure.argtypes + [c_p]
+        L.lie_closure_dev.restype = ctypes.c_int
+        L.lie_closure_batched.argtypes = [ctypes.c_int, ctypes.POINTER(c_p), ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.POINTER(c_p),
+                                          ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Options),
+                                          ctypes.POINTER(Report)]
+        L.lie_closure_batched.restype = ctypes.c_int
+        L.lc_split_gemm_f32.argtypes = [c_p, c_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_p, c_p]
+        L.lc_split_gemm_f32.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().lc_status_string(int(status)).decode()
+
+
+def version() -> str:
+    return lib().lc_version().decode()
+
+
+def make_options(precision="mixed", **kw) -> Options:
+    o = Options()
+    lib().lc_default_options(ctypes.byref(o))
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class ClosureResult:
+    dim: int
+    basis: np.ndarray | None
+    status: int
+    report: dict
+
+
+def _check(status: int, check: bool):
+    if check and status != LC_OK:
+        raise LieClosureError(status, status_string(status))
+
+
+def lie_closure(generators, tol: float, max_dim: int | None = None, return_basis: bool = True,
+                check: bool = True, precision="mixed", **opts) -> ClosureResult:
+    """Algorithm 4 on host arrays: ``generators`` is (k, d, d) complex128."""
+    g = np.ascontiguousarray(generators, dtype=np.complex128)
+    if g.ndim != 3 or g.shape[1] != g.shape[2]:
+        raise ValueError("generators must have shape (k, d, d)")
+    k, d, _ = g.shape
+    cap = int(max_dim) if max_dim is not None else d * d
+    basis = np.zeros((cap, d, d), dtype=np.complex128) if return_basis else None
+    dim = ctypes.c_longlong(0)
+    rep = Report()
+    o = make_options(precision, **opts)
+    st = lib().lie_closure(g.ctypes.data, k, d, float(tol), basis.ctypes.data if basis is not None else None,
+                           ctypes.byref(dim), cap, ctypes.byref(o), ctypes.byref(rep))
+    _check(st, check)
+    n = int(dim.value)
+    return ClosureResult(n, basis[:n] if basis is not None else None, st, rep.as_dict())
+
+
+def lie_closure_dev(generators, tol: float, max_dim: int | None = None, basis_out=None, stream=None,
+                    check: bool = True, precision="mixed", **opts) -> ClosureResult:
+    """Algorithm 4 on device tensors (torch complex128 on the current CUDA device).
+
+    ``basis_out`` (optional) is a (max_dim, d, d) complex128 device tensor that
+    receives the basis; ``stream`` a torch.cuda.Stream (default: current)."""
+    import torch
+    g = generators
+    if not (g.is_cuda and g.dtype == torch.complex128 and g.is_contiguous() and g.dim() == 3):
+        raise ValueError("generators must be a contiguous (k, d, d) complex128 CUDA tensor")
+    k, d, _ = g.shape
+    cap = int(max_dim) if max_dim is not None else d * d
+    if basis_out is not None:
+        if not (basis_out.is_cuda and basis_out.dtype == torch.complex128 and basis_out.is_contiguous()
+                and basis_out.shape[0] >= cap and tuple(basis_out.shape[1:]) == (d, d)):
+            raise ValueError("basis_out must be a contiguous (max_dim, d, d) complex128 CUDA tensor")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    dim = ctypes.c_longlong(0)
+    rep = Report()
+    o = make_options(precision, **opts)
+    st = lib().lie_closure_dev(g.data_ptr(), k, d, float(tol),
+                               basis_out.data_ptr() if basis_out is not None else None, ctypes.byref(dim), cap,
+                               ctypes.byref(o), ctypes.byref(rep), ctypes.c_void_p(s.cuda_stream))
+    _check(st, check)
+    return ClosureResult(int(dim.value), None, st, rep.as_dict())
+
+
+def lie_closure_batched(generator_sets, tol: float, max_dims=None, return_basis: bool = False,
+                        precision="mixed", **opts):
+    """Algorithm 4 on many independent sets; returns (dims, statuses, bases, reports)."""
+    sets = [np.ascontiguousarray(g, dtype=np.complex128) for g in generator_sets]
+    n = len(sets)
+    ks = (ctypes.c_int * n)(*[g.shape[0] for g in sets])
+    ds = (ctypes.c_int * n)(*[g.shape[1] for g in sets])
+    caps = [int(max_dims[i]) if max_dims is not None else sets[i].shape[1] ** 2 for i in range(n)]
+    cap_arr = (ctypes.c_longlong * n)(*caps)
+    gptr = (ctypes.c_void_p * n)(*[g.ctypes.data for g in sets])
+    bases = [np.zeros((caps[i], sets[i].shape[1], sets[i].shape[1]), dtype=np.complex128) for i in range(n)] \
+        if return_basis else None
+    bptr = (ctypes.c_void_p * n)(*[b.ctypes.data for b in bases]) if bases is not None else None
+    dims = (ctypes.c_longlong * n)()
+    stat = (ctypes.c_int * n)()
+    reps = (Report * n)()
+    o = make_options(precision, **opts)
+    lib().lie_closure_batched(n, gptr, ks, ds, float(tol), bptr, cap_arr, dims, stat, ctypes.byref(o), reps)
+    dims_l = [int(x) for x in dims]
+    out_b = [bases[i][:dims_l[i]] for i in range(n)] if bases is not None else None
+    return dims_l, [int(x) for x in stat], out_b, [r.as_dict() for r in reps]
+
+
+def lc_split_gemm_f32(A, B, stream=None):
+    """D = A B^T (torch FP32 CUDA tensors) through the split-BF16 tcgen05 GEMM."""
+    import torch
+    if not (A.is_cuda and B.is_cuda and A.dtype == torch.float32 and B.dtype == torch.float32):
+        raise ValueError("A and B must be float32 CUDA tensors")
+    A = A.contiguous()
+    B = B.contiguous()
+    M, K = A.shape
+    N, K2 = B.shape
+    if K != K2:
+        raise ValueError("inner dimensions differ")
+    D = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = lib().lc_split_gemm_f32(A.data_ptr(), B.data_ptr(), M, N, K, D.data_ptr(), ctypes.c_void_p(s.cuda_stream))
+    _check(st, True)
+    return D

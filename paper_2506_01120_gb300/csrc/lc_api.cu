@@ -1,0 +1,644 @@
+// Host driver and C ABI of the Lie-closure library.
+//
+// The driver runs Algorithm 4 of arXiv 2506.01120 (Section 3.2) in candidate
+// blocks.  The basis V lives on the device as packed FP64 rows (see
+// lc_internal.cuh); a block is a contiguous run of the pair sweep
+// (l, m), m < l, l ascending then m ascending, restricted to l < |V| at the
+// start of the block.  Each block is screened in one pass (FP64, or split-BF16
+// tensor-core GEMMs in mixed mode); screened-in candidates are recomputed in
+// FP64, orthogonalised twice against V, and then tested and appended one by
+// one in pair order against V plus this block's earlier accepts -- the same
+// decisions the sequential algorithm takes, since a block's brackets involve
+// only elements that existed before the block.
+#include "lc_internal.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+using namespace lc;
+
+namespace {
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+// ------------------------------------------------------------ memory pool
+cudaError_t get_pool(cudaMemPool_t* out) {
+  static std::mutex mu;
+  static std::vector<cudaMemPool_t> pools;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> g(mu);
+  if ((int)pools.size() <= dev) pools.resize(dev + 1, nullptr);
+  if (!pools[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p;
+    e = cudaMemPoolCreate(&p, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = ~0ull;   // keep freed blocks for the next call
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = p;
+  }
+  *out = pools[dev];
+  return cudaSuccess;
+}
+
+// One allocation carved into 256-byte aligned pieces.
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0, cap = 0;
+  cudaStream_t s = nullptr;
+  bool planning = true;
+  template <typename T>
+  T* take(size_t n) {
+    off = (off + 255) & ~size_t(255);
+    T* p = planning ? nullptr : reinterpret_cast<T*>(base + off);
+    off += n * sizeof(T) + 256;
+    return p;
+  }
+  cudaError_t allocate(cudaStream_t st) {
+    s = st;
+    cap = off;
+    cudaMemPool_t pool;
+    cudaError_t e = get_pool(&pool);
+    if (e != cudaSuccess) return e;
+    e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&base), cap, pool, s);
+    off = 0;
+    planning = false;
+    return e;
+  }
+  ~Arena() {
+    if (base) cudaFreeAsync(base, s);
+  }
+};
+
+#define LC_TRY(x)                                                  \
+  do {                                                             \
+    cudaError_t e_ = (x);                                          \
+    if (e_ != cudaSuccess) {                                       \
+      if (opt.verbose)                                             \
+        fprintf(stderr, "lieclosure: %s at %s:%d\n", cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return e_ == cudaErrorMemoryAllocation ? LC_ERR_OOM : LC_ERR_CUDA; \
+    }                                                              \
+  } while (0)
+
+struct HostMirror {
+  DevStats stats;
+  DevStatus st;
+  double maxdev, maxabs;
+  int nonfinite;
+};
+
+class Closure {
+ public:
+  Closure(int k, int d, double tol, long long ncap, const lc_options& o, cudaStream_t s)
+      : k_(k), d_(d), tol_(tol), ncap_(ncap), opt(o), s_(s) {
+    P_ = d * d;
+    mixed_ = (o.precision == LC_PREC_MIXED_BF16X3);
+    ldp_ = round_up(P_, 128);
+    ncap_pad_ = (int)round_up_ll(ncap_, 128);
+    int K = o.block_k > 0 ? o.block_k : 2048;
+    // bound the candidate buffers to about 3 GB
+    const double per = mixed_ ? (8.0 * ldp_ + 4.0 * ldp_ + 4.0 * ncap_pad_ + 8.0 * ncap_)
+                              : (24.0 * ldp_ + 8.0 * ncap_);
+    const int kmem = (int)std::max(1.0, std::min(1.0e9, 3.0e9 / per));
+    K = std::min(K, kmem);
+    K = std::max(K, k_);         // the generator pass is one block
+    K_ = std::max(1, K);
+    Kpad_ = round_up(K_, 128);
+    tau_ = o.tau_screen > 0 ? o.tau_screen : 1e-3;
+    eta_ = o.eta_abs > 0 ? o.eta_abs : 1e-12;
+    eta_screen_ = std::max(eta_, 1e-5);
+  }
+
+  int run(const double2* d_gens, double2* d_basis_out, long long* dim_out, lc_report* rep) {
+    const double t_start = now_s();
+    t_last_accept_ = 0.0;
+    int rc = setup(d_gens);
+    if (rc == LC_OK) rc = generator_pass();
+    if (rc == LC_OK) rc = sweep();
+    if (rc == LC_OK || rc == LC_ERR_CAPACITY) {
+      if (d_basis_out && N_ > 0) {
+        cudaError_t e = unpack_basis(V64_, (int)N_, d_, ldp_, d_basis_out, s_);
+        if (e != cudaSuccess) rc = LC_ERR_CUDA;
+      }
+    }
+    cudaError_t e = cudaStreamSynchronize(s_);
+    if (e != cudaSuccess && rc == LC_OK) rc = LC_ERR_CUDA;
+    if (dim_out) *dim_out = N_;
+    if (rep) {
+      memset(rep, 0, sizeof(*rep));
+      rep->dim = N_;
+      rep->brackets_checked = checked_;
+      rep->generators_checked = k_;
+      rep->n_nonzero = nonzero_;
+      rep->n_flagged = flagged_;
+      rep->n_blocks = blocks_;
+      int l = 1, m = 0;
+      if (t_ > 0) pair_from_index(t_, &l, &m);
+      rep->cursor_l = l;
+      rep->cursor_m = m;
+      rep->t_total_s = now_s() - t_start;
+      rep->t_last_accept_s = t_last_accept_ > 0 ? t_last_accept_ - t_start : 0.0;
+      double mn = 0.0, mx = 0.0;
+      if (host_) {
+        memcpy(&mn, &host_->stats.min_acc_bits, 8);
+        memcpy(&mx, &host_->stats.max_rej_bits, 8);
+      }
+      rep->min_acc_rel_res = mn;
+      rep->max_rej_rel_res = mx;
+      rep->tau_screen = mixed_ ? tau_ : 0.5 * tol_;
+      double sr = 0.0;
+      if (host_) memcpy(&sr, &host_->stats.max_screen_rej_bits, 8);
+      rep->max_screen_rej_rel_res = sr;
+      rep->kernel_launches = launches_ + 1 + (N_ > 0 && d_basis_out ? 1 : 0);
+      rep->gemm_launches = gemm_launches_;
+      rep->gemm_flops = gemm_flops_;
+      destroy_events();
+      for (int i = 0; i < 6; ++i) rep->t_phase_s[i] = t_phase_[i];
+      rep->precision = opt.precision;
+      rep->status = rc;
+    }
+    return rc;
+  }
+
+  ~Closure() {
+    destroy_events();
+    if (host_) cudaFreeHost(host_);
+  }
+
+ private:
+  int k_, d_, P_, ldp_, ncap_pad_, K_, Kpad_;
+  double tol_, tau_, eta_, eta_screen_;
+  long long ncap_;
+  lc_options opt;
+  cudaStream_t s_;
+  bool mixed_;
+  Arena ar_;
+  HostMirror* host_ = nullptr;
+  long long N_ = 0, t_ = 0, checked_ = 0, nonzero_ = 0, flagged_ = 0, blocks_ = 0;
+  double t_last_accept_ = 0.0;
+  // device buffers
+  double *G64_ = nullptr, *V64_ = nullptr, *H64_ = nullptr, *S64_ = nullptr, *R64_ = nullptr, *beta64_ = nullptr;
+  double *hn2_ = nullptr, *rn2_ = nullptr, *hnf_ = nullptr, *rnf_ = nullptr, *chk_ = nullptr;
+  int *idx_ = nullptr, *nonfinite_ = nullptr;
+  DevStats* stats_ = nullptr;
+  DevStatus* st_ = nullptr;
+  __nv_bfloat16 *Vhi_ = nullptr, *Vlo_ = nullptr, *VThi_ = nullptr, *VTlo_ = nullptr;
+  __nv_bfloat16 *Hhi_ = nullptr, *Hlo_ = nullptr, *Bhi_ = nullptr, *Blo_ = nullptr;
+  float *hn2f_ = nullptr, *rn2f_ = nullptr;
+
+  void carve() {
+    G64_ = ar_.take<double>((size_t)k_ * ldp_);
+    V64_ = ar_.take<double>((size_t)ncap_ * ldp_);
+    R64_ = ar_.take<double>((size_t)K_ * ldp_);
+    beta64_ = ar_.take<double>((size_t)K_ * ncap_);
+    hnf_ = ar_.take<double>(K_);
+    rnf_ = ar_.take<double>(K_);
+    idx_ = ar_.take<int>(K_);
+    stats_ = ar_.take<DevStats>(1);
+    st_ = ar_.take<DevStatus>(1);
+    chk_ = ar_.take<double>(2);
+    nonfinite_ = ar_.take<int>(1);
+    if (!mixed_) {
+      H64_ = ar_.take<double>((size_t)K_ * ldp_);
+      S64_ = ar_.take<double>((size_t)K_ * ldp_);
+      hn2_ = ar_.take<double>(K_);
+      rn2_ = ar_.take<double>(K_);
+    } else {
+      Vhi_ = ar_.take<__nv_bfloat16>((size_t)ncap_pad_ * ldp_);
+      Vlo_ = ar_.take<__nv_bfloat16>((size_t)ncap_pad_ * ldp_);
+      VThi_ = ar_.take<__nv_bfloat16>((size_t)ldp_ * ncap_pad_);
+      VTlo_ = ar_.take<__nv_bfloat16>((size_t)ldp_ * ncap_pad_);
+      Hhi_ = ar_.take<__nv_bfloat16>((size_t)Kpad_ * ldp_);
+      Hlo_ = ar_.take<__nv_bfloat16>((size_t)Kpad_ * ldp_);
+      Bhi_ = ar_.take<__nv_bfloat16>((size_t)Kpad_ * ncap_pad_);
+      Blo_ = ar_.take<__nv_bfloat16>((size_t)Kpad_ * ncap_pad_);
+      hn2f_ = ar_.take<float>(Kpad_);
+      rn2f_ = ar_.take<float>(Kpad_);
+    }
+  }
+
+  int sync_read() {
+    cudaError_t e = cudaMemcpyAsync(&host_->stats, stats_, sizeof(DevStats), cudaMemcpyDeviceToHost, s_);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&host_->st, st_, sizeof(DevStatus), cudaMemcpyDeviceToHost, s_);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s_);
+    if (e != cudaSuccess) return LC_ERR_CUDA;
+    collect_phases();
+    if (host_->st.code != 0) {
+      if (opt.verbose)
+        fprintf(stderr, "lieclosure: device status %d at site %d (info %lld)\n", host_->st.code, host_->st.where,
+                host_->st.info);
+      return host_->st.code;
+    }
+    return LC_OK;
+  }
+
+  int setup(const double2* d_gens) {
+    carve();
+    LC_TRY(cudaHostAlloc(reinterpret_cast<void**>(&host_), sizeof(HostMirror), cudaHostAllocDefault));
+    LC_TRY(ar_.allocate(s_));
+    carve();
+    if (mixed_) {
+      if (!tcgen05_available()) return LC_ERR_CUDA;
+      // zero padding rows/columns once; kernels only ever write live regions
+      LC_TRY(cudaMemsetAsync(Vhi_, 0, sizeof(__nv_bfloat16) * (size_t)ncap_pad_ * ldp_, s_));
+      LC_TRY(cudaMemsetAsync(Vlo_, 0, sizeof(__nv_bfloat16) * (size_t)ncap_pad_ * ldp_, s_));
+      LC_TRY(cudaMemsetAsync(VThi_, 0, sizeof(__nv_bfloat16) * (size_t)ldp_ * ncap_pad_, s_));
+      LC_TRY(cudaMemsetAsync(VTlo_, 0, sizeof(__nv_bfloat16) * (size_t)ldp_ * ncap_pad_, s_));
+      LC_TRY(cudaMemsetAsync(Hhi_, 0, sizeof(__nv_bfloat16) * (size_t)Kpad_ * ldp_, s_));
+      LC_TRY(cudaMemsetAsync(Hlo_, 0, sizeof(__nv_bfloat16) * (size_t)Kpad_ * ldp_, s_));
+      LC_TRY(cudaMemsetAsync(Bhi_, 0, sizeof(__nv_bfloat16) * (size_t)Kpad_ * ncap_pad_, s_));
+      LC_TRY(cudaMemsetAsync(Blo_, 0, sizeof(__nv_bfloat16) * (size_t)Kpad_ * ncap_pad_, s_));
+    }
+    if (ldp_ > P_) {
+      // padding columns of the FP64 rows stay zero
+      LC_TRY(cudaMemset2DAsync(V64_ + P_, sizeof(double) * ldp_, 0, sizeof(double) * (ldp_ - P_), ncap_, s_));
+    }
+    LC_TRY(cudaMemsetAsync(st_, 0, sizeof(DevStatus), s_));
+    LC_TRY(cudaMemsetAsync(stats_, 0, sizeof(DevStats), s_));
+    {
+      // min_acc starts at +inf
+      DevStats init;
+      memset(&init, 0, sizeof(init));
+      double inf = INFINITY;
+      memcpy(&init.min_acc_bits, &inf, 8);
+      host_->stats = init;
+      LC_TRY(cudaMemcpyAsync(stats_, &host_->stats, sizeof(DevStats), cudaMemcpyHostToDevice, s_));
+    }
+    LC_TRY(cudaMemsetAsync(chk_, 0, 2 * sizeof(double), s_));
+    LC_TRY(cudaMemsetAsync(nonfinite_, 0, sizeof(int), s_));
+    LC_TRY(pack_generators(d_gens, k_, d_, ldp_, G64_, chk_, chk_ + 1, nonfinite_, s_));
+    LC_TRY(cudaMemcpyAsync(&host_->maxdev, chk_, 2 * sizeof(double), cudaMemcpyDeviceToHost, s_));
+    LC_TRY(cudaMemcpyAsync(&host_->nonfinite, nonfinite_, sizeof(int), cudaMemcpyDeviceToHost, s_));
+    LC_TRY(cudaStreamSynchronize(s_));
+    if (host_->nonfinite) return LC_ERR_NONFINITE;
+    if (host_->maxdev > 1e-12 * host_->maxabs) return LC_ERR_NOT_ANTIHERMITIAN;
+    if (opt.saturation_exit) {
+      // largest possible dimension: d^2 - 1, plus the trace direction
+      std::vector<double> diag((size_t)k_ * d_);
+      LC_TRY(cudaMemcpy2DAsync(diag.data(), sizeof(double), G64_, sizeof(double) * (d_ + 1), sizeof(double),
+                               (size_t)d_, cudaMemcpyDeviceToHost, s_));
+      // the 2-D copy above walks one generator's diagonal; repeat per generator
+      for (int q = 1; q < k_; ++q)
+        LC_TRY(cudaMemcpy2DAsync(diag.data() + (size_t)q * d_, sizeof(double), G64_ + (size_t)q * ldp_,
+                                 sizeof(double) * (d_ + 1), sizeof(double), (size_t)d_, cudaMemcpyDeviceToHost,
+                                 s_));
+      LC_TRY(cudaStreamSynchronize(s_));
+      bool trace = false;
+      for (int q = 0; q < k_; ++q) {
+        double t = 0.0, a = 0.0;
+        for (int j = 0; j < d_; ++j) {
+          t += diag[(size_t)q * d_ + j];
+          a = std::max(a, std::fabs(diag[(size_t)q * d_ + j]));
+        }
+        if (std::fabs(t) > 1e-12 * std::max(1.0, a * d_)) trace = true;
+      }
+      dmax_ = (long long)d_ * d_ - 1 + (trace ? 1 : 0);
+    }
+    return LC_OK;
+  }
+
+  long long dmax_ = -1;
+
+  // ---------------------------------------------------- phase timing
+  // With opt.profile each phase is bracketed by CUDA events on the call's
+  // stream; elapsed times are collected after the next synchronisation.
+  enum { PH_BRACKET = 0, PH_GEMM1 = 1, PH_GEMM2 = 2, PH_SCREEN = 3, PH_ACCEPT = 4, PH_OTHER = 5 };
+  struct Pending { int phase; cudaEvent_t a, b; };
+  std::vector<cudaEvent_t> ev_pool_;
+  std::vector<Pending> pending_;
+  double t_phase_[6] = {0, 0, 0, 0, 0, 0};
+  long long launches_ = 0, gemm_launches_ = 0;
+  double gemm_flops_ = 0.0;
+  cudaEvent_t ev_open_ = nullptr;
+
+  cudaEvent_t get_ev() {
+    if (!ev_pool_.empty()) {
+      cudaEvent_t e = ev_pool_.back();
+      ev_pool_.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void ph_begin() {
+    if (!opt.profile) return;
+    ev_open_ = get_ev();
+    cudaEventRecord(ev_open_, s_);
+  }
+  void ph_end(int phase) {
+    if (!opt.profile) return;
+    cudaEvent_t b = get_ev();
+    cudaEventRecord(b, s_);
+    pending_.push_back({phase, ev_open_, b});
+  }
+  void collect_phases() {
+    for (auto& p : pending_) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) t_phase_[p.phase] += ms * 1e-3;
+      ev_pool_.push_back(p.a);
+      ev_pool_.push_back(p.b);
+    }
+    pending_.clear();
+  }
+  void destroy_events() {
+    collect_phases();
+    for (auto e : ev_pool_) cudaEventDestroy(e);
+    ev_pool_.clear();
+  }
+
+  // Test-and-append of the f candidate rows in R64 (FP64, pair order).
+  int accept_rows(int f) {
+    flagged_ += f;
+    ph_begin();
+    LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, hnf_, s_));
+    const int n0 = (int)N_;
+    if (n0 > 0) {
+      for (int pass = 0; pass < 2; ++pass) {
+        LC_TRY(gemm_nt_f64(f, n0, P_, R64_, ldp_, V64_, ldp_, beta64_, (int)ncap_, s_));
+        LC_TRY(gemm_nn_sub_f64(f, P_, n0, beta64_, (int)ncap_, V64_, ldp_, R64_, ldp_, s_));
+      }
+      launches_ += 4;
+    }
+    LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, rnf_, s_));
+    LC_TRY(zero_stats(stats_, n0, s_));
+    for (int i = 0; i < f; ++i)
+      LC_TRY(accept_step(i, f, R64_, ldp_, rnf_, hnf_, tol_, eta_ * eta_, V64_, ldp_, (int)ncap_, P_, stats_, st_,
+                         nullptr, s_));
+    launches_ += 3 + f;
+    ph_end(PH_ACCEPT);
+    int rc = sync_read();
+    const long long n1 = host_->stats.ncur;
+    if (n1 > N_) t_last_accept_ = now_s();
+    if (mixed_ && n1 > n0) {
+      ph_begin();
+      LC_TRY(split_rows(V64_, ldp_, n0, (int)n1, P_, Vhi_, Vlo_, ldp_, VThi_, VTlo_, ncap_pad_, s_));
+      ph_end(PH_OTHER);
+      launches_ += 1;
+    }
+    N_ = n1;
+    return rc;
+  }
+
+  int generator_pass() {
+    LC_TRY(cudaMemcpy2DAsync(R64_, sizeof(double) * ldp_, G64_, sizeof(double) * ldp_, sizeof(double) * P_, k_,
+                             cudaMemcpyDeviceToDevice, s_));
+    return accept_rows(k_);
+  }
+
+  int after_screen(long long t0) {
+    int rc = sync_read();
+    if (rc != LC_OK) return rc;
+    nonzero_ += host_->stats.nnonzero;
+    const int f = host_->stats.nflag;
+    if (f > 0) {
+      if (mixed_) {
+        ph_begin();
+        LC_TRY(bracket_fp64(V64_, d_, ldp_, t0, idx_, f, R64_, ldp_, s_));
+        ph_end(PH_ACCEPT);
+      } else {
+        LC_TRY(gather_rows_f64(H64_, ldp_, idx_, f, P_, R64_, ldp_, s_));
+      }
+      launches_ += 1;
+      return accept_rows(f);
+    }
+    return LC_OK;
+  }
+
+  int block_fp64(long long t0, int kb) {
+    ph_begin();
+    LC_TRY(bracket_fp64(V64_, d_, ldp_, t0, nullptr, kb, H64_, ldp_, s_));
+    ph_end(PH_BRACKET);
+    ph_begin();
+    LC_TRY(rownorm2_f64(kb, P_, H64_, ldp_, hn2_, s_));
+    LC_TRY(gemm_nt_f64(kb, (int)N_, P_, H64_, ldp_, V64_, ldp_, beta64_, (int)ncap_, s_));
+    ph_end(PH_GEMM1);
+    ph_begin();
+    LC_TRY(cudaMemcpy2DAsync(S64_, sizeof(double) * ldp_, H64_, sizeof(double) * ldp_, sizeof(double) * P_, kb,
+                             cudaMemcpyDeviceToDevice, s_));
+    LC_TRY(gemm_nn_sub_f64(kb, P_, (int)N_, beta64_, (int)ncap_, V64_, ldp_, S64_, ldp_, s_));
+    LC_TRY(rownorm2_f64(kb, P_, S64_, ldp_, rn2_, s_));
+    ph_end(PH_GEMM2);
+    // one FP64 projection pass: ||r1|| <= tol/2 ||h|| implies the two-pass
+    // residual is below tol ||h|| as well, so such candidates are dependent
+    const double tau = 0.5 * tol_;
+    ph_begin();
+    LC_TRY(screen_compact_f64(hn2_, rn2_, kb, eta_ * eta_, tau * tau, idx_, stats_, s_));
+    ph_end(PH_SCREEN);
+    launches_ += 6;
+    return after_screen(t0);
+  }
+
+  int block_mixed(long long t0, int kb) {
+    ph_begin();
+    LC_TRY(bracket_mixed(V64_, d_, ldp_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, s_));
+    ph_end(PH_BRACKET);
+    const int M = round_up(kb, 128);
+    const int Npad = round_up((int)N_, 128);
+    SplitGemmArgs g1;
+    memset(&g1, 0, sizeof(g1));
+    g1.Ahi = Hhi_;
+    g1.Alo = Hlo_;
+    g1.Bhi = Vhi_;
+    g1.Blo = Vlo_;
+    g1.M = M;
+    g1.N = Npad;
+    g1.K = ldp_;
+    g1.lda = ldp_;
+    g1.ldb = ldp_;
+    g1.Dhi = Bhi_;
+    g1.Dlo = Blo_;
+    g1.ldd = ncap_pad_;
+    g1.epilogue = 0;
+    g1.spin_cap = opt.spin_cap;
+    g1.st = st_;
+    ph_begin();
+    LC_TRY(split_gemm_tcgen05(g1, s_));
+    ph_end(PH_GEMM1);
+    SplitGemmArgs g2;
+    memset(&g2, 0, sizeof(g2));
+    g2.Ahi = Bhi_;
+    g2.Alo = Blo_;
+    g2.Bhi = VThi_;
+    g2.Blo = VTlo_;
+    g2.M = M;
+    g2.N = ldp_;
+    g2.K = Npad;
+    g2.lda = ncap_pad_;
+    g2.ldb = ncap_pad_;
+    g2.Hhi = Hhi_;
+    g2.Hlo = Hlo_;
+    g2.ldh = ldp_;
+    g2.rn2 = rn2f_;
+    g2.epilogue = 1;
+    g2.spin_cap = opt.spin_cap;
+    g2.st = st_;
+    LC_TRY(cudaMemsetAsync(rn2f_, 0, sizeof(float) * M, s_));
+    ph_begin();
+    LC_TRY(split_gemm_tcgen05(g2, s_));
+    ph_end(PH_GEMM2);
+    gemm_launches_ += 2;
+    gemm_flops_ += 2.0 * 6.0 * (double)kb * (double)N_ * (double)P_;
+    const float es = (float)eta_screen_, ts = (float)tau_;
+    ph_begin();
+    LC_TRY(screen_compact_f32(hn2f_, rn2f_, kb, es * es, ts * ts, idx_, stats_, s_));
+    ph_end(PH_SCREEN);
+    launches_ += 4;
+    return after_screen(t0);
+  }
+
+  int sweep() {
+    t_ = 0;
+    for (;;) {
+      const long long T = pairs_below(N_);
+      if (t_ >= T) break;
+      if (dmax_ >= 0 && N_ >= dmax_) break;
+      long long kb = std::min<long long>(K_, T - t_);
+      if (opt.max_candidates > 0) kb = std::min<long long>(kb, opt.max_candidates - checked_);
+      if (kb <= 0) break;
+      const long long n_before = N_;
+      int rc = mixed_ ? block_mixed(t_, (int)kb) : block_fp64(t_, (int)kb);
+      ++blocks_;
+      t_ += kb;
+      checked_ += kb;
+      if (opt.verbose)
+        fprintf(stderr, "lieclosure: block %lld t=%lld kb=%lld flagged=%d dim %lld -> %lld\n", blocks_, t_ - kb, kb,
+                host_ ? host_->stats.nflag : -1, n_before, N_);
+      if (rc != LC_OK) return rc;
+    }
+    return LC_OK;
+  }
+};
+
+int check_args(const void* g, int k, int d, double tol, long long max_dim, const lc_options& o) {
+  if (!g || k < 1 || d < 2 || !(tol > 0.0) || max_dim < 1) return LC_ERR_ARG;
+  if (o.precision != LC_PREC_FP64 && o.precision != LC_PREC_MIXED_BF16X3) return LC_ERR_ARG;
+  if (o.block_k < 0 || o.tau_screen < 0 || o.eta_abs < 0 || o.max_candidates < 0) return LC_ERR_ARG;
+  if ((long long)d * d > (1ll << 31) / 2) return LC_ERR_ARG;
+  return LC_OK;
+}
+
+int closure_device(const double2* d_gens, int k, int d, double tol, double2* d_basis, long long* dim_out,
+                   long long max_dim, const lc_options& o, lc_report* rep, cudaStream_t s) {
+  const long long ncap = std::min<long long>(max_dim, (long long)d * d);
+  Closure c(k, d, tol, ncap, o, s);
+  int rc = c.run(d_gens, d_basis, dim_out, rep);
+  if (rc == LC_OK && max_dim < (long long)d * d && dim_out && *dim_out > max_dim) rc = LC_ERR_CAPACITY;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lc_default_options(lc_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = LC_PREC_MIXED_BF16X3;
+  o->eta_abs = 1e-12;
+  o->tau_screen = 1e-3;
+  o->block_k = 0;
+  o->saturation_exit = 0;
+  o->spin_cap = 0;
+  o->max_candidates = 0;
+  o->verbose = 0;
+  o->profile = 0;
+}
+
+const char* lc_status_string(int s) {
+  switch (s) {
+    case LC_OK: return "ok";
+    case LC_ERR_ARG: return "invalid argument";
+    case LC_ERR_NOT_ANTIHERMITIAN: return "generator is not anti-Hermitian";
+    case LC_ERR_NONFINITE: return "non-finite value in the generators";
+    case LC_ERR_CAPACITY: return "basis capacity (max_dim) exceeded";
+    case LC_ERR_CUDA: return "CUDA error";
+    case LC_ERR_OOM: return "out of device memory";
+    case LC_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+const char* lc_version(void) { return "lieclosure-gb300 0.1 (sm_103a)"; }
+
+int lie_closure_dev(const lc_c128* generators, int k, int d, double tol, lc_c128* basis_out, long long* dim_out,
+                    long long max_dim, const lc_options* opt, lc_report* rep, void* stream) {
+  lc_options o;
+  if (opt) o = *opt; else lc_default_options(&o);
+  if (dim_out) *dim_out = 0;
+  int rc = check_args(generators, k, d, tol, max_dim, o);
+  if (rc != LC_OK) return rc;
+  return closure_device(reinterpret_cast<const double2*>(generators), k, d, tol,
+                        reinterpret_cast<double2*>(basis_out), dim_out, max_dim, o, rep,
+                        static_cast<cudaStream_t>(stream));
+}
+
+int lie_closure(const lc_c128* generators, int k, int d, double tol, lc_c128* basis_out, long long* dim_out,
+                long long max_dim, const lc_options* opt, lc_report* rep) {
+  lc_options o;
+  if (opt) o = *opt; else lc_default_options(&o);
+  if (dim_out) *dim_out = 0;
+  int rc = check_args(generators, k, d, tol, max_dim, o);
+  if (rc != LC_OK) return rc;
+  cudaStream_t s;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return LC_ERR_CUDA;
+  const size_t gbytes = sizeof(double2) * (size_t)k * d * d;
+  const long long ncap = std::min<long long>(max_dim, (long long)d * d);
+  const size_t bbytes = basis_out ? sizeof(double2) * (size_t)ncap * d * d : 0;
+  double2 *dg = nullptr, *db = nullptr;
+  cudaMemPool_t pool;
+  rc = LC_OK;
+  if (get_pool(&pool) != cudaSuccess) rc = LC_ERR_CUDA;
+  if (rc == LC_OK && cudaMallocFromPoolAsync(reinterpret_cast<void**>(&dg), gbytes, pool, s) != cudaSuccess)
+    rc = LC_ERR_OOM;
+  if (rc == LC_OK && bbytes &&
+      cudaMallocFromPoolAsync(reinterpret_cast<void**>(&db), bbytes, pool, s) != cudaSuccess)
+    rc = LC_ERR_OOM;
+  if (rc == LC_OK && cudaMemcpyAsync(dg, generators, gbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    rc = LC_ERR_CUDA;
+  long long dim = 0;
+  if (rc == LC_OK) rc = closure_device(dg, k, d, tol, db, &dim, max_dim, o, rep, s);
+  if ((rc == LC_OK || rc == LC_ERR_CAPACITY) && db && dim > 0) {
+    if (cudaMemcpyAsync(basis_out, db, sizeof(double2) * (size_t)std::min(dim, ncap) * d * d,
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      rc = LC_ERR_CUDA;
+  }
+  if (dg) cudaFreeAsync(dg, s);
+  if (db) cudaFreeAsync(db, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && rc == LC_OK) rc = LC_ERR_CUDA;
+  cudaStreamDestroy(s);
+  if (dim_out) *dim_out = dim;
+  return rc;
+}
+
+int lie_closure_batched(int nsets, const lc_c128* const* generators, const int* k, const int* d, double tol,
+                        lc_c128* const* basis_out, const long long* max_dim, long long* dim_out, int* status_out,
+                        const lc_options* opt, lc_report* rep) {
+  if (nsets < 0 || (nsets > 0 && (!generators || !k || !d || !max_dim))) return LC_ERR_ARG;
+  int first = LC_OK;
+  for (int s = 0; s < nsets; ++s) {
+    long long dim = 0;
+    int rc = lie_closure(generators[s], k[s], d[s], tol, basis_out ? basis_out[s] : nullptr, &dim, max_dim[s], opt,
+                         rep ? rep + s : nullptr);
+    if (dim_out) dim_out[s] = dim;
+    if (status_out) status_out[s] = rc;
+    if (rc != LC_OK && first == LC_OK) first = rc;
+  }
+  return first;
+}
+
+}  // extern "C"

@@ -1,0 +1,129 @@
+// Internal declarations shared by the library's translation units.
+//
+// Packed representation (used by every kernel): an anti-Hermitian a = iH is
+// stored as P = d*d reals S, row-major d x d:
+//   S[j][j] = H[j][j] / sqrt(d)
+//   S[j][k] = sqrt(2/d) * Re H[j][k]   (j < k)
+//   S[k][j] = sqrt(2/d) * Im H[j][k]   (j < k)
+// With this scaling the paper's inner product <a, b> = tr(a^dagger b)/d
+// (Section 2.2) is the plain dot product of the packed rows, so an
+// orthonormal basis V is a matrix with orthonormal rows and the projection of
+// Section 3.2 is two ordinary GEMMs.  tr(a^dagger b) is real for anti-Hermitian
+// a and b, so real coefficients suffice and real and complex linear
+// independence coincide.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "../../include/lieclosure.h"
+
+namespace lc {
+
+// Device-side error word: the first failing check wins.
+struct DevStatus {
+  int code;            // lc_status value, 0 = ok
+  int where;           // kernel-specific site id
+  long long info;      // e.g. the spin iteration count or an index
+};
+
+enum : int {
+  SITE_NONE = 0,
+  SITE_ACCEPT_CAPACITY = 1,
+  SITE_GEMM_TMA_WAIT = 2,
+  SITE_GEMM_MMA_WAIT = 3,
+  SITE_GEMM_EPI_WAIT = 4,
+};
+
+// Accept-path statistics kept on the device (doubles stored by bit pattern so
+// that integer atomicMin/atomicMax order them; all values are >= 0).
+struct DevStats {
+  unsigned long long min_acc_bits;
+  unsigned long long max_rej_bits;
+  unsigned long long max_screen_rej_bits;  // largest screened rel. residual among screen rejects
+  int ncur;            // current |V| (rows of the FP64 basis)
+  int naccepted;       // accepts in the current block
+  int nflag;           // flagged candidates in the current block
+  int nnonzero;        // candidates above the norm floor in the current block
+};
+
+// pair index t = l(l-1)/2 + m, 0 <= m < l  <->  (l, m)
+__host__ __device__ inline void pair_from_index(long long t, int* l, int* m) {
+  long long L = (long long)((1.0 + sqrt(1.0 + 8.0 * (double)t)) * 0.5);
+  while (L * (L - 1) / 2 > t) --L;
+  while ((L + 1) * L / 2 <= t) ++L;
+  *l = (int)L;
+  *m = (int)(t - L * (L - 1) / 2);
+}
+
+inline long long pairs_below(long long n) { return n * (n - 1) / 2; }
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+inline long long round_up_ll(long long x, long long m) { return (x + m - 1) / m * m; }
+
+// ------------------------------------------------------------ FP64 kernels
+// (lc_fp64.cu)
+cudaError_t pack_generators(const double2* g, int k, int d, int ldp, double* out,
+                            double* dev_maxdev, double* dev_maxabs, int* dev_nonfinite,
+                            cudaStream_t s);
+cudaError_t unpack_basis(const double* V, int n, int d, int ldp, double2* out, cudaStream_t s);
+// brackets of pairs t0 + i, i = 0 .. count-1 (or t0 + idx[i] when idx is
+// given), packed into rows of out (row stride ldo)
+cudaError_t bracket_fp64(const double* V, int d, int ldv, long long t0, const int* idx,
+                         int count, double* out, int ldo, cudaStream_t s);
+// C = A * B^T (BT) or C = C - A * B (!BT); row-major, FP64
+cudaError_t gemm_nt_f64(int M, int N, int K, const double* A, int lda, const double* B, int ldb,
+                        double* C, int ldc, cudaStream_t s);
+cudaError_t gemm_nn_sub_f64(int M, int N, int K, const double* A, int lda, const double* B,
+                            int ldb, double* C, int ldc, cudaStream_t s);
+cudaError_t rownorm2_f64(int M, int N, const double* A, int lda, double* out, cudaStream_t s);
+cudaError_t gather_rows_f64(const double* src, int lds, const int* idx, int count, int ncols,
+                            double* dst, int ldd, cudaStream_t s);
+// flags candidates with hn2 > eta^2 and rn2 > tau^2 hn2; writes the flagged
+// candidate positions in order to idx and their count to stats->nflag
+cudaError_t screen_compact_f64(const double* hn2, const double* rn2, int count, double eta2,
+                               double tau2, int* idx, DevStats* stats, cudaStream_t s);
+cudaError_t screen_compact_f32(const float* hn2, const float* rn2, int count, float eta2,
+                               float tau2, int* idx, DevStats* stats, cudaStream_t s);
+// sequential in-block accept for flagged row i (see lc_fp64.cu)
+cudaError_t accept_step(int i, int f, double* R, int ldr, double* rn2, const double* hn2,
+                        double tol, double eta2, double* V, int ldv, int ncap, int P,
+                        DevStats* stats, DevStatus* st, int* accepted_rows, cudaStream_t s);
+cudaError_t zero_stats(DevStats* stats, int ncur, cudaStream_t s);
+
+// ------------------------------------------------------ mixed-precision path
+// (lc_mixed.cu)
+// FP64 rows [r0, r1) of V -> split BF16 copies (row-major and transposed)
+cudaError_t split_rows(const double* V, int ldv, int r0, int r1, int P,
+                       __nv_bfloat16* Vhi, __nv_bfloat16* Vlo, int ldvs,
+                       __nv_bfloat16* VThi, __nv_bfloat16* VTlo, int ldvt, cudaStream_t s);
+// brackets of pairs t0..t0+count-1 in FP32, written as split BF16 rows plus
+// FP32 squared norms
+cudaError_t bracket_mixed(const double* V, int d, int ldv, long long t0, int count,
+                          __nv_bfloat16* Hhi, __nv_bfloat16* Hlo, int ldh, float* hn2,
+                          cudaStream_t s);
+
+// tcgen05 split-BF16 GEMMs (lc_tcgen05.cu).  All operands K-major BF16.
+// D[M x N] = Ahi*Bhi^T + Ahi*Blo^T + Alo*Bhi^T with FP32 accumulation.
+struct SplitGemmArgs {
+  const __nv_bfloat16 *Ahi, *Alo;  // M x K, row stride lda (elements)
+  const __nv_bfloat16 *Bhi, *Blo;  // N x K, row stride ldb
+  int M, N, K, lda, ldb;           // M % 128 == 0, N % BN == 0, K % 64 == 0
+  // epilogue 0: store split BF16 of D to Dhi/Dlo (row stride ldd)
+  __nv_bfloat16 *Dhi, *Dlo;
+  int ldd;
+  // epilogue 1: rn2[m] += sum_n (H[m][n] - D[m][n])^2 with H = Hhi + Hlo (stride ldh)
+  const __nv_bfloat16 *Hhi, *Hlo;
+  int ldh;
+  float* rn2;
+  float* Df32;                     // epilogue 2: plain FP32 store (tests)
+  int epilogue;
+  long long spin_cap;
+  DevStatus* st;
+};
+cudaError_t split_gemm_tcgen05(const SplitGemmArgs& a, cudaStream_t s);
+bool tcgen05_available();
+
+}  // namespace lc

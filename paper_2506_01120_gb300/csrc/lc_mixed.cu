@@ -1,0 +1,168 @@
+// Mixed-precision helpers of the screening path:
+//  * split_rows    -- new FP64 basis rows -> BF16 hi/lo copies, row-major
+//                     (operand of the projection beta = H V^T) and transposed
+//                     (operand of the residual R = H - beta V);
+//  * bracket_mixed -- brackets of a block of pairs in FP32, written as split
+//                     BF16 candidate rows plus FP32 squared norms.
+#include "lc_internal.cuh"
+
+namespace lc {
+namespace {
+
+__device__ __forceinline__ void split_bf16(double x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __double2bfloat16(x);
+  lo = __double2bfloat16(x - (double)__bfloat162float(hi));
+}
+
+__device__ __forceinline__ void split_bf16f(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// 32 x 32 tiles: coalesced reads of V rows, coalesced writes of both copies.
+__global__ void k_split_rows(const double* __restrict__ V, int ldv, int r0, int r1, int P,
+                             __nv_bfloat16* __restrict__ Vhi, __nv_bfloat16* __restrict__ Vlo, int ldvs,
+                             __nv_bfloat16* __restrict__ VThi, __nv_bfloat16* __restrict__ VTlo, int ldvt) {
+  __shared__ __nv_bfloat16 th[32][33], tl[32][33];
+  const int p0 = blockIdx.x * 32, i0 = r0 + blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int i = i0 + yy, p = p0 + tx;
+    __nv_bfloat16 hi = __float2bfloat16_rn(0.f), lo = hi;
+    if (i < r1 && p < P) {
+      split_bf16(V[(long long)i * ldv + p], hi, lo);
+      Vhi[(long long)i * ldvs + p] = hi;
+      Vlo[(long long)i * ldvs + p] = lo;
+    }
+    th[yy][tx] = hi;
+    tl[yy][tx] = lo;
+  }
+  __syncthreads();
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int p = p0 + yy, i = i0 + tx;
+    if (i < r1 && p < P) {
+      VThi[(long long)p * ldvt + i] = th[tx][yy];
+      VTlo[(long long)p * ldvt + i] = tl[tx][yy];
+    }
+  }
+}
+
+// FP32 bracket: same tiling as the FP64 kernel (tile pair (I, J), I <= J).
+constexpr int BT = 32;
+constexpr int BQ = 16;
+
+__device__ __forceinline__ float2 herm_elem_f(const double* __restrict__ S, int d, int r, int c, double s1, double s2) {
+  if (r >= d || c >= d) return make_float2(0.f, 0.f);
+  if (r == c) return make_float2((float)(S[(long long)r * d + r] * s1), 0.f);
+  if (r < c) return make_float2((float)(S[(long long)r * d + c] * s2), (float)(S[(long long)c * d + r] * s2));
+  return make_float2((float)(S[(long long)c * d + r] * s2), (float)(-S[(long long)r * d + c] * s2));
+}
+
+__device__ __forceinline__ void cmacf(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+
+__global__ void __launch_bounds__(256) k_bracket_mixed(const double* __restrict__ V, int d, int ldv, long long t0,
+                                                       __nv_bfloat16* __restrict__ Hhi, __nv_bfloat16* __restrict__ Hlo,
+                                                       int ldh, float* __restrict__ hn2) {
+  __shared__ float2 sAI[BT][BQ + 1], sAJ[BT][BQ + 1], sBI[BQ][BT + 1], sBJ[BQ][BT + 1];
+  __shared__ float red[8];
+  const int pair = blockIdx.y;
+  int l, m;
+  pair_from_index(t0 + pair, &l, &m);
+  const double* SA = V + (long long)l * ldv;
+  const double* SB = V + (long long)m * ldv;
+  const int nt = (d + BT - 1) / BT;
+  int tp = blockIdx.x, I = 0;
+  while (tp >= nt - I) { tp -= nt - I; ++I; }
+  const int J = I + tp;
+  const double s1 = sqrt((double)d), s2 = sqrt((double)d / 2.0);
+  const int tid = threadIdx.x;
+  const int jj = tid >> 3, kk0 = (tid & 7) * 4;
+  float2 c1[4], c2[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) { c1[u] = make_float2(0.f, 0.f); c2[u] = make_float2(0.f, 0.f); }
+  for (int q0 = 0; q0 < d; q0 += BQ) {
+    for (int e = tid; e < BT * BQ; e += 256) {
+      const int r = e / BQ, c = e % BQ;
+      sAI[r][c] = herm_elem_f(SA, d, I * BT + r, q0 + c, s1, s2);
+      sAJ[r][c] = herm_elem_f(SA, d, J * BT + r, q0 + c, s1, s2);
+      const int rb = e / BT, cb = e % BT;
+      sBI[rb][cb] = herm_elem_f(SB, d, q0 + rb, I * BT + cb, s1, s2);
+      sBJ[rb][cb] = herm_elem_f(SB, d, q0 + rb, J * BT + cb, s1, s2);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int q = 0; q < BQ; ++q) {
+      const float2 a1 = sAI[jj][q];
+      const float2 b2 = sBI[q][jj];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        cmacf(c1[u], a1, sBJ[q][kk0 + u]);
+        cmacf(c2[u], sAJ[kk0 + u][q], b2);
+      }
+    }
+    __syncthreads();
+  }
+  __nv_bfloat16* Oh = Hhi + (long long)pair * ldh;
+  __nv_bfloat16* Ol = Hlo + (long long)pair * ldh;
+  const float o1 = (float)(1.0 / sqrt((double)d)), o2 = (float)sqrt(2.0 / (double)d);
+  float ss = 0.f;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int j = I * BT + jj, k = J * BT + kk0 + u;
+    if (j >= d || k >= d) continue;
+    __nv_bfloat16 hi, lo;
+    if (j < k) {
+      const float re = -(c1[u].y + c2[u].y) * o2;
+      const float im = (c1[u].x - c2[u].x) * o2;
+      split_bf16f(re, hi, lo);
+      Oh[(long long)j * d + k] = hi;
+      Ol[(long long)j * d + k] = lo;
+      split_bf16f(im, hi, lo);
+      Oh[(long long)k * d + j] = hi;
+      Ol[(long long)k * d + j] = lo;
+      ss = fmaf(re, re, fmaf(im, im, ss));
+    } else if (j == k) {
+      const float dg = -2.f * c1[u].y * o1;
+      split_bf16f(dg, hi, lo);
+      Oh[(long long)j * d + j] = hi;
+      Ol[(long long)j * d + j] = lo;
+      ss = fmaf(dg, dg, ss);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if ((tid & 31) == 0) red[tid >> 5] = ss;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.f;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    atomicAdd(&hn2[pair], t);
+  }
+}
+
+}  // namespace
+
+cudaError_t split_rows(const double* V, int ldv, int r0, int r1, int P, __nv_bfloat16* Vhi, __nv_bfloat16* Vlo,
+                       int ldvs, __nv_bfloat16* VThi, __nv_bfloat16* VTlo, int ldvt, cudaStream_t s) {
+  if (r1 <= r0) return cudaSuccess;
+  dim3 grid((P + 31) / 32, (r1 - r0 + 31) / 32);
+  k_split_rows<<<grid, 256, 0, s>>>(V, ldv, r0, r1, P, Vhi, Vlo, ldvs, VThi, VTlo, ldvt);
+  return cudaGetLastError();
+}
+
+cudaError_t bracket_mixed(const double* V, int d, int ldv, long long t0, int count, __nv_bfloat16* Hhi,
+                          __nv_bfloat16* Hlo, int ldh, float* hn2, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(hn2, 0, sizeof(float) * count, s);
+  if (e != cudaSuccess) return e;
+  const int nt = (d + BT - 1) / BT;
+  dim3 grid(nt * (nt + 1) / 2, count);
+  k_bracket_mixed<<<grid, 256, 0, s>>>(V, d, ldv, t0, Hhi, Hlo, ldh, hn2);
+  return cudaGetLastError();
+}
+
+}  // namespace lc

@@ -1,0 +1,475 @@
+// Split-BF16 GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+//   D[M x N] = Ahi Bhi^T + Ahi Blo^T + Alo Bhi^T      (FP32 accumulation in TMEM)
+//
+// where X = Xhi + Xlo is the two-term BF16 split of an FP32/FP64 operand
+// (Markidis et al. 2018; Henry, Tang and Heinecke 2019).  The dropped
+// Alo Blo^T term and the split remainders leave a relative error near 2^-16
+// per product, which is what the screening step budgets for.
+//
+// Both operands are K-major BF16 in global memory.  Each CTA owns one
+// 128 x BN output tile.  Warp 0 (one lane) streams the four operand tiles of
+// each 64-wide k-slice into shared memory with TMA (128-byte swizzle); warp 1
+// (one lane) issues the three tcgen05.mma per 16-wide k-step into a TMEM
+// accumulator and frees each stage with tcgen05.commit; afterwards all four
+// warps read their 32 TMEM lanes (rows) back with tcgen05.ld and run the
+// epilogue.  Every mbarrier wait is bounded by a wall-clock limit; on expiry
+// the kernel records LC_ERR_TIMEOUT, drains what it issued and returns.
+#include "lc_internal.cuh"
+#include "../../include/lieclosure_kernels.h"
+
+#include <cuda.h>
+#include <cstring>
+#include <mutex>
+
+namespace lc {
+namespace {
+
+constexpr int BM = 128;
+constexpr int BN = 128;
+constexpr int BK = 64;                       // 64 BF16 = 128 bytes = one swizzle row
+constexpr int STAGES = 3;
+constexpr int TILE_A_BYTES = BM * BK * 2;    // 16 KB
+constexpr int TILE_B_BYTES = BN * BK * 2;    // 16 KB
+constexpr int STAGE_BYTES = 2 * TILE_A_BYTES + 2 * TILE_B_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;   // + alignment slack
+constexpr int TMEM_COLS = BN;                // FP32 accumulator columns
+constexpr int NTHREADS = 128;
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait: true on success, false once limit_ns has elapsed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0 && globaltimer_ns() - t0 > limit_ns) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major operand tile with 128-byte swizzle: rows of 128 bytes, 8-row groups
+// 1024 bytes apart (stride byte offset), leading byte offset unused (1),
+// descriptor version 1 (bits 46-47), swizzle mode 2 = 128B (bits 61-63).
+__device__ __forceinline__ uint64_t make_sw128_desc(uint32_t saddr) {
+  uint64_t desc = 0;
+  desc |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  desc |= (uint64_t)1u << 16;                  // LBO (ignored for swizzled K-major)
+  desc |= (uint64_t)(1024u >> 4) << 32;        // SBO
+  desc |= (uint64_t)1u << 46;                  // version
+  desc |= (uint64_t)2u << 61;                  // SWIZZLE_128B
+  return desc;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and B
+// BF16 (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22,
+// M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t make_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_32cols(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ void record_timeout(DevStatus* st, int where, long long info) {
+  if (st && atomicCAS(&st->code, 0, (int)LC_ERR_TIMEOUT) == 0) {
+    st->where = where;
+    st->info = info;
+  }
+}
+
+struct GemmParams {
+  int M, N, K;
+  __nv_bfloat16 *Dhi, *Dlo;
+  int ldd;
+  const __nv_bfloat16 *Hhi, *Hlo;
+  int ldh;
+  float* rn2;
+  float* Df32;
+  int epilogue;
+  uint64_t limit_ns;
+  DevStatus* st;
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_split_gemm(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+                 const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
+                 const GemmParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+  const int nk = p.K / BK;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- producer: TMA
+    int issued = 0;
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+      if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1u, p.limit_ns)) {
+        record_timeout(p.st, SITE_GEMM_TMA_WAIT, kt);
+        abort_flag = 1;
+        break;
+      }
+      if (*(volatile int*)&abort_flag) break;
+      uint8_t* st = smem + s * STAGE_BYTES;
+      mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+      const int kx = kt * BK;
+      tma_load_2d(st, &mAhi, &full_bar[s], kx, m0);
+      tma_load_2d(st + TILE_A_BYTES, &mAlo, &full_bar[s], kx, m0);
+      tma_load_2d(st + 2 * TILE_A_BYTES, &mBhi, &full_bar[s], kx, n0);
+      tma_load_2d(st + 2 * TILE_A_BYTES + TILE_B_BYTES, &mBlo, &full_bar[s], kx, n0);
+      issued = kt + 1;
+    }
+    // drain: wait (bounded) until every issued stage has landed, so no copy
+    // is still writing shared memory when the CTA exits
+    for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt) {
+      const int s = kt % STAGES;
+      mbar_wait_bounded(&full_bar[s], (uint32_t)(kt / STAGES) & 1u, p.limit_ns);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = make_idesc_bf16(BM, BN);
+    bool ok = true;
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+      if (!mbar_wait_bounded(&full_bar[s], ph, p.limit_ns)) {
+        record_timeout(p.st, SITE_GEMM_MMA_WAIT, kt);
+        abort_flag = 1;
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a_hi = smem_u32(smem + s * STAGE_BYTES);
+      const uint32_t a_lo = a_hi + TILE_A_BYTES;
+      const uint32_t b_hi = a_hi + 2 * TILE_A_BYTES;
+      const uint32_t b_lo = b_hi + TILE_B_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint32_t off = kk * 32;   // 16 BF16 along K inside the swizzled row
+        const uint64_t dAh = make_sw128_desc(a_hi + off), dAl = make_sw128_desc(a_lo + off);
+        const uint64_t dBh = make_sw128_desc(b_hi + off), dBl = make_sw128_desc(b_lo + off);
+        mma_bf16(tmem, dAh, dBh, idesc, (kt | kk) ? 1u : 0u);
+        mma_bf16(tmem, dAh, dBl, idesc, 1u);
+        mma_bf16(tmem, dAl, dBh, idesc, 1u);
+      }
+      mma_commit(&empty_bar[s]);     // stage s is free once these MMAs retire
+    }
+    (void)ok;
+    mma_commit(&done_bar);           // accumulator complete (or drained on abort)
+  }
+  __syncwarp();
+
+  // ---------------- epilogue: all four warps
+  const bool have = mbar_wait_bounded(&done_bar, 0u, p.limit_ns);
+  if (!have) {
+    record_timeout(p.st, SITE_GEMM_EPI_WAIT, blockIdx.y * gridDim.x + blockIdx.x);
+    atomicExch(&abort_flag, 1);
+  }
+  __syncthreads();                   // makes the run decision uniform across the CTA
+  tc_fence_after();
+  const bool run = !(*(volatile int*)&abort_flag);
+  const int row = m0 + warp * 32 + lane;
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  float acc2 = 0.0f;
+  if (run) {
+    for (int c = 0; c < BN; c += 32) {
+      float v[32];
+      tmem_ld_32cols(trow + (uint32_t)c, v);     // warp-collective
+      if (row < p.M) {
+        const int col = n0 + c;
+        if (p.epilogue == 0) {
+          __align__(16) __nv_bfloat16 hi[32], lo[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            hi[i] = __float2bfloat16_rn(v[i]);
+            lo[i] = __float2bfloat16_rn(v[i] - __bfloat162float(hi[i]));
+          }
+          uint4* dh = reinterpret_cast<uint4*>(p.Dhi + (long long)row * p.ldd + col);
+          uint4* dl = reinterpret_cast<uint4*>(p.Dlo + (long long)row * p.ldd + col);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            dh[i] = reinterpret_cast<const uint4*>(hi)[i];
+            dl[i] = reinterpret_cast<const uint4*>(lo)[i];
+          }
+        } else if (p.epilogue == 1) {
+          const uint4* hh = reinterpret_cast<const uint4*>(p.Hhi + (long long)row * p.ldh + col);
+          const uint4* hl = reinterpret_cast<const uint4*>(p.Hlo + (long long)row * p.ldh + col);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const uint4 a = hh[i], b = hl[i];
+            const __nv_bfloat16* ah = reinterpret_cast<const __nv_bfloat16*>(&a);
+            const __nv_bfloat16* bl = reinterpret_cast<const __nv_bfloat16*>(&b);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const float r = (__bfloat162float(ah[e]) + __bfloat162float(bl[e])) - v[i * 8 + e];
+              acc2 = fmaf(r, r, acc2);
+            }
+          }
+        } else {
+          float4* o = reinterpret_cast<float4*>(p.Df32 + (long long)row * p.ldd + col);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        }
+      }
+    }
+    if (p.epilogue == 1 && row < p.M) atomicAdd(&p.rn2[row], acc2);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ------------------------------------------------------------ host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  });
+  return fn;
+}
+
+// 2-D BF16 map: rows x cols (cols contiguous, row stride ld elements),
+// box = box_rows x 64 with 128-byte swizzle.
+bool make_map(CUtensorMap* m, const __nv_bfloat16* base, long long rows, long long cols, long long ld,
+              int box_rows) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides, box,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool tcgen05_available() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3 && get_encode() != nullptr;
+}
+
+cudaError_t split_gemm_tcgen05(const SplitGemmArgs& a, cudaStream_t s) {
+  if (a.M <= 0 || a.N <= 0) return cudaSuccess;
+  if (a.M % BM || a.N % BN || a.K % BK || a.K <= 0) return cudaErrorInvalidValue;
+  if ((a.lda % 64) || (a.ldb % 64)) return cudaErrorInvalidValue;
+  CUtensorMap mAhi, mAlo, mBhi, mBlo;
+  if (!make_map(&mAhi, a.Ahi, a.M, a.K, a.lda, BM) || !make_map(&mAlo, a.Alo, a.M, a.K, a.lda, BM) ||
+      !make_map(&mBhi, a.Bhi, a.N, a.K, a.ldb, BN) || !make_map(&mBlo, a.Blo, a.N, a.K, a.ldb, BN))
+    return cudaErrorInvalidValue;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_split_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  GemmParams p;
+  p.M = a.M;
+  p.N = a.N;
+  p.K = a.K;
+  p.Dhi = a.Dhi;
+  p.Dlo = a.Dlo;
+  p.ldd = a.ldd;
+  p.Hhi = a.Hhi;
+  p.Hlo = a.Hlo;
+  p.ldh = a.ldh;
+  p.rn2 = a.rn2;
+  p.Df32 = a.Df32;
+  p.epilogue = a.epilogue;
+  p.limit_ns = a.spin_cap > 0 ? (uint64_t)a.spin_cap : 4000000000ull;
+  p.st = a.st;
+  dim3 grid(a.N / BN, a.M / BM);
+  k_split_gemm<<<grid, NTHREADS, SMEM_BYTES, s>>>(mAhi, mAlo, mBhi, mBlo, p);
+  return cudaGetLastError();
+}
+
+}  // namespace lc
+
+// ------------------------------------------------ unit-level entry point
+namespace lc {
+namespace {
+
+__global__ void k_split_pad_f32(const float* __restrict__ X, int rows, int cols, int rows_pad, int cols_pad,
+                                __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  const long long tot = (long long)rows_pad * cols_pad;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / cols_pad), c = (int)(e % cols_pad);
+    const float x = (r < rows && c < cols) ? X[(long long)r * cols + c] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[e] = h;
+    lo[e] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
+
+__global__ void k_crop_f32(const float* __restrict__ Dp, int ldp, int M, int N, float* __restrict__ D) {
+  const long long tot = (long long)M * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / N), c = (int)(e % N);
+    D[e] = Dp[(long long)r * ldp + c];
+  }
+}
+
+}  // namespace
+}  // namespace lc
+
+extern "C" LC_API int lc_split_gemm_f32(const float* A, const float* B, int M, int N, int K, float* D,
+                                        void* stream) {
+  using namespace lc;
+  if (!A || !B || !D || M < 1 || N < 1 || K < 1) return LC_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!tcgen05_available()) return LC_ERR_CUDA;
+  const int Mp = round_up(M, BM), Np = round_up(N, BN), Kp = round_up(K, BK);
+  const size_t nA = (size_t)Mp * Kp, nB = (size_t)Np * Kp, nD = (size_t)Mp * Np;
+  char* ws = nullptr;
+  const size_t bytes = 4 * ((nA + nB) * 2 + 256) + nD * 4 + sizeof(DevStatus) + 1024;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&ws), bytes, s) != cudaSuccess) return LC_ERR_OOM;
+  size_t off = 0;
+  auto take = [&](size_t b) { char* p = ws + off; off = (off + b + 255) & ~size_t(255); return p; };
+  __nv_bfloat16* Ahi = reinterpret_cast<__nv_bfloat16*>(take(nA * 2));
+  __nv_bfloat16* Alo = reinterpret_cast<__nv_bfloat16*>(take(nA * 2));
+  __nv_bfloat16* Bhi = reinterpret_cast<__nv_bfloat16*>(take(nB * 2));
+  __nv_bfloat16* Blo = reinterpret_cast<__nv_bfloat16*>(take(nB * 2));
+  float* Dp = reinterpret_cast<float*>(take(nD * 4));
+  DevStatus* st = reinterpret_cast<DevStatus*>(take(sizeof(DevStatus)));
+  int rc = LC_OK;
+  DevStatus hst;
+  memset(&hst, 0, sizeof(hst));
+  if (cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess) rc = LC_ERR_CUDA;
+  if (rc == LC_OK) {
+    k_split_pad_f32<<<1024, 256, 0, s>>>(A, M, K, Mp, Kp, Ahi, Alo);
+    k_split_pad_f32<<<1024, 256, 0, s>>>(B, N, K, Np, Kp, Bhi, Blo);
+    SplitGemmArgs g;
+    memset(&g, 0, sizeof(g));
+    g.Ahi = Ahi; g.Alo = Alo; g.Bhi = Bhi; g.Blo = Blo;
+    g.M = Mp; g.N = Np; g.K = Kp; g.lda = Kp; g.ldb = Kp;
+    g.Df32 = Dp; g.ldd = Np; g.epilogue = 2; g.st = st;
+    if (split_gemm_tcgen05(g, s) != cudaSuccess) rc = LC_ERR_CUDA;
+  }
+  if (rc == LC_OK) {
+    k_crop_f32<<<1024, 256, 0, s>>>(Dp, Np, M, N, D);
+    if (cudaGetLastError() != cudaSuccess) rc = LC_ERR_CUDA;
+    cudaMemcpyAsync(&hst, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
+  }
+  cudaFreeAsync(ws, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && rc == LC_OK) rc = LC_ERR_CUDA;
+  if (rc == LC_OK && hst.code != 0) rc = hst.code;
+  return rc;
+}

@@ -1,0 +1,73 @@
+"""The C ABI library loads and exports every symbol the public headers declare
+(no GPU needed; no compute call is made)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2506_01120_gb300 import binding
+from paper_2506_01120_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def built_lib():
+    if not os.path.exists(binding.LIB_PATH):
+        build()
+    return binding.lib()
+
+
+def declared_symbols():
+    names = []
+    for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        text = open(h).read()
+        names += re.findall(r"LC_API\s+[\w\s\*]+?\b(\w+)\s*\(", text)
+    return names
+
+
+def test_headers_declare_the_boundary():
+    names = declared_symbols()
+    for required in ("lie_closure", "lie_closure_dev", "lie_closure_batched"):
+        assert required in names
+    assert sorted(names) == sorted(binding.EXPORTED)
+
+
+def test_every_declared_symbol_is_exported(built_lib):
+    for name in declared_symbols():
+        assert hasattr(built_lib, name), name
+        assert ctypes.cast(getattr(built_lib, name), ctypes.c_void_p).value
+
+
+def test_host_only_calls(built_lib):
+    o = binding.make_options("fp64")
+    assert o.precision == binding.LC_PREC_FP64
+    assert o.eta_abs == 1e-12 and o.tau_screen == 1e-3 and o.saturation_exit == 0
+    assert binding.status_string(binding.LC_ERR_CAPACITY).startswith("basis capacity")
+    assert binding.status_string(12345) == "unknown status"
+    assert "sm_103a" in binding.version()
+
+
+def test_struct_layouts_match_header():
+    """ctypes mirrors of lc_options / lc_report have the C sizes."""
+    assert ctypes.sizeof(binding.Options) == 4 + 4 + 8 + 8 + 4 + 4 + 8 + 8 + 4 + 4
+    assert ctypes.sizeof(binding.Report) == 8 * 8 + 8 * 5 + 8 + 8 + 8 + 8 + 8 * 6 + 4 * 2
+
+
+def test_argument_errors_need_no_gpu(built_lib):
+    """Invalid arguments are rejected on the host before any CUDA call."""
+    import numpy as np
+    g = np.zeros((1, 4, 4), dtype=np.complex128)
+    dim = ctypes.c_longlong(7)
+    L = built_lib
+    assert L.lie_closure(None, 1, 4, 1e-8, None, ctypes.byref(dim), 16, None, None) == binding.LC_ERR_ARG
+    assert dim.value == 0
+    assert L.lie_closure(g.ctypes.data, 0, 4, 1e-8, None, ctypes.byref(dim), 16, None, None) == binding.LC_ERR_ARG
+    assert L.lie_closure(g.ctypes.data, 1, 4, -1.0, None, ctypes.byref(dim), 16, None, None) == binding.LC_ERR_ARG
+    assert L.lie_closure(g.ctypes.data, 1, 4, 1e-8, None, ctypes.byref(dim), 0, None, None) == binding.LC_ERR_ARG
+    o = binding.make_options("fp64")
+    o.precision = 7
+    assert L.lie_closure(g.ctypes.data, 1, 4, 1e-8, None, ctypes.byref(dim), 16, ctypes.byref(o), None) \
+        == binding.LC_ERR_ARG

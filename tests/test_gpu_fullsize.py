@@ -1,0 +1,83 @@
+"""GPU parity at full workload sizes, through properties that hold at any
+size plus sampled checks the oracle computes one by one."""
+import numpy as np
+import pytest
+
+import oracle.closure as oc
+from paper_2506_01120_gb300 import binding, inputs
+from paper_2506_01120_gb300.build import build
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    build()
+
+
+def _pauli_label_of(v, n):
+    """The Pauli string P with v = c i P, c = +-1, or None."""
+    d = v.shape[0]
+    H = -1j * v
+    # a Pauli string has exactly one nonzero per row, all of modulus 1
+    nz = np.abs(H) > 1e-9
+    if not np.all(nz.sum(axis=1) == 1) or not np.allclose(np.abs(H[nz]), 1.0, atol=1e-12):
+        return None
+    best = None
+    for lab in _candidate_labels(H, n):
+        P = inputs.pauli_matrix(lab)
+        c = np.vdot(P, H) / d
+        if abs(abs(c) - 1) < 1e-12 and np.allclose(H, c * P, atol=1e-12):
+            best = lab
+    return best
+
+
+def _candidate_labels(H, n):
+    # x bits from the permutation pattern of row 0; z bits from the phases
+    d = H.shape[0]
+    col = int(np.argmax(np.abs(H[0])))
+    x = col
+    labels = []
+    for z in range(d):
+        lab = []
+        for q in range(n):
+            xb = (x >> (n - 1 - q)) & 1
+            zb = (z >> (n - 1 - q)) & 1
+            lab.append("IXZY"[xb + 2 * zb])
+        labels.append("".join(lab))
+    return labels
+
+
+@pytest.mark.parametrize("prec", ["mixed"])
+def test_su64_chain_full(prec):
+    g, labels = inputs.workload_generators("su64_chain_d64")
+    r = binding.lie_closure(g, 1e-8, precision=prec)
+    assert r.dim == 4095
+    D = r.dim
+    assert r.report["brackets_checked"] == D * (D - 1) // 2
+    V = r.basis
+    assert oc.ortho_defect(V) < 1e-12
+    rng = np.random.default_rng(7)
+    pairs = [tuple(sorted(rng.choice(D, size=2, replace=False), reverse=True)) for _ in range(300)]
+    assert oc.closure_residual(V, pairs=pairs) < 1e-7
+    # every element is +-i times one Pauli string, and the strings are exactly
+    # the exact integer closure of the generator strings
+    want = set(oc.pauli_closure(labels))
+    rows = rng.choice(D, size=200, replace=False)
+    for i in rows:
+        lab = _pauli_label_of(V[i], 6)
+        assert lab in want
+    traces = np.einsum("nii->n", V)
+    assert np.max(np.abs(traces)) < 1e-12
+
+
+def test_su128_random_growth_mixed():
+    """Two random generators at d = 128 reach su(128) (dim 16383); the run stops
+    at saturation, the exact dimension argument for anti-Hermitian inputs."""
+    g, _ = inputs.workload_generators("su128_random2_d128")
+    r = binding.lie_closure(g, 1e-8, precision="mixed", saturation_exit=1, return_basis=False)
+    assert r.dim == 16383
+    assert r.report["min_acc_rel_res"] > 1e-8
