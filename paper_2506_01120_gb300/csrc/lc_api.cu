@@ -121,6 +121,7 @@ class Closure {
     tau_ = o.tau_screen > 0 ? o.tau_screen : 1e-3;
     eta_ = o.eta_abs > 0 ? o.eta_abs : 1e-12;
     eta_screen_ = std::max(eta_, 1e-5);
+    tc_bracket_ = mixed_ && bracket_tc_supported(d);
   }
 
   int run(const double2* d_gens, double2* d_basis_out, long long* dim_out, lc_report* rep) {
@@ -198,7 +199,10 @@ class Closure {
   DevStatus* st_ = nullptr;
   __nv_bfloat16 *Vhi_ = nullptr, *Vlo_ = nullptr, *VThi_ = nullptr, *VTlo_ = nullptr;
   __nv_bfloat16 *Hhi_ = nullptr, *Hlo_ = nullptr, *Bhi_ = nullptr, *Blo_ = nullptr;
-  float *hn2f_ = nullptr, *rn2f_ = nullptr;
+  __nv_bfloat16 *Chi_ = nullptr, *Clo_ = nullptr, *Ehi_ = nullptr, *Elo_ = nullptr;
+  float *hn2f_ = nullptr, *rn2f_ = nullptr, *hn2c_ = nullptr;
+  int *nz_idx_ = nullptr, *nnz_ = nullptr;
+  bool tc_bracket_ = false;
 
   void carve() {
     G64_ = ar_.take<double>((size_t)k_ * ldp_);
@@ -228,6 +232,16 @@ class Closure {
       Blo_ = ar_.take<__nv_bfloat16>((size_t)Kpad_ * ncap_pad_);
       hn2f_ = ar_.take<float>(Kpad_);
       rn2f_ = ar_.take<float>(Kpad_);
+      Chi_ = ar_.take<__nv_bfloat16>((size_t)Kpad_ * ldp_);
+      Clo_ = ar_.take<__nv_bfloat16>((size_t)Kpad_ * ldp_);
+      hn2c_ = ar_.take<float>(Kpad_);
+      nz_idx_ = ar_.take<int>(Kpad_);
+      nnz_ = ar_.take<int>(1);
+      if (tc_bracket_) {
+        const size_t R = 2 * (size_t)d_;
+        Ehi_ = ar_.take<__nv_bfloat16>((size_t)ncap_ * R * R);
+        Elo_ = ar_.take<__nv_bfloat16>((size_t)ncap_ * R * R);
+      }
     }
   }
 
@@ -262,6 +276,8 @@ class Closure {
       LC_TRY(cudaMemsetAsync(Hlo_, 0, sizeof(__nv_bfloat16) * (size_t)Kpad_ * ldp_, s_));
       LC_TRY(cudaMemsetAsync(Bhi_, 0, sizeof(__nv_bfloat16) * (size_t)Kpad_ * ncap_pad_, s_));
       LC_TRY(cudaMemsetAsync(Blo_, 0, sizeof(__nv_bfloat16) * (size_t)Kpad_ * ncap_pad_, s_));
+      LC_TRY(cudaMemsetAsync(Chi_, 0, sizeof(__nv_bfloat16) * (size_t)Kpad_ * ldp_, s_));
+      LC_TRY(cudaMemsetAsync(Clo_, 0, sizeof(__nv_bfloat16) * (size_t)Kpad_ * ldp_, s_));
     }
     if (ldp_ > P_) {
       // padding columns of the FP64 rows stay zero
@@ -387,8 +403,12 @@ class Closure {
     if (mixed_ && n1 > n0) {
       ph_begin();
       LC_TRY(split_rows(V64_, ldp_, n0, (int)n1, P_, Vhi_, Vlo_, ldp_, VThi_, VTlo_, ncap_pad_, s_));
-      ph_end(PH_OTHER);
       launches_ += 1;
+      if (tc_bracket_) {
+        LC_TRY(build_embedding(V64_, ldp_, n0, (int)n1, d_, Ehi_, Elo_, s_));
+        launches_ += 1;
+      }
+      ph_end(PH_OTHER);
     }
     N_ = n1;
     return rc;
@@ -404,6 +424,7 @@ class Closure {
     int rc = sync_read();
     if (rc != LC_OK) return rc;
     nonzero_ += host_->stats.nnonzero;
+    if (mixed_) gemm_flops_ += 2.0 * 6.0 * (double)host_->stats.nnonzero * (double)N_ * (double)P_;
     const int f = host_->stats.nflag;
     if (f > 0) {
       if (mixed_) {
@@ -445,17 +466,29 @@ class Closure {
 
   int block_mixed(long long t0, int kb) {
     ph_begin();
-    LC_TRY(bracket_mixed(V64_, d_, ldp_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, s_));
+    if (tc_bracket_) {
+      LC_TRY(bracket_tc(Ehi_, Elo_, ncap_, d_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, opt.spin_cap, st_, s_));
+    } else {
+      LC_TRY(bracket_mixed(V64_, d_, ldp_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, s_));
+    }
     ph_end(PH_BRACKET);
+    // candidates with a (numerically) zero bracket are rejected outright; the
+    // rest are packed into consecutive rows so the GEMMs skip the zeros
+    const float es = (float)eta_screen_, ts = (float)tau_;
+    ph_begin();
+    LC_TRY(compact_nonzero(hn2f_, kb, es * es, nz_idx_, nnz_, s_));
+    LC_TRY(gather_candidates(Hhi_, Hlo_, ldp_, hn2f_, nz_idx_, nnz_, kb, ldp_, Chi_, Clo_, hn2c_, s_));
+    ph_end(PH_SCREEN);
     const int M = round_up(kb, 128);
     const int Npad = round_up((int)N_, 128);
     SplitGemmArgs g1;
     memset(&g1, 0, sizeof(g1));
-    g1.Ahi = Hhi_;
-    g1.Alo = Hlo_;
+    g1.Ahi = Chi_;
+    g1.Alo = Clo_;
     g1.Bhi = Vhi_;
     g1.Blo = Vlo_;
     g1.M = M;
+    g1.Mdev = nnz_;
     g1.N = Npad;
     g1.K = ldp_;
     g1.lda = ldp_;
@@ -476,12 +509,13 @@ class Closure {
     g2.Bhi = VThi_;
     g2.Blo = VTlo_;
     g2.M = M;
+    g2.Mdev = nnz_;
     g2.N = ldp_;
     g2.K = Npad;
     g2.lda = ncap_pad_;
     g2.ldb = ncap_pad_;
-    g2.Hhi = Hhi_;
-    g2.Hlo = Hlo_;
+    g2.Hhi = Chi_;
+    g2.Hlo = Clo_;
     g2.ldh = ldp_;
     g2.rn2 = rn2f_;
     g2.epilogue = 1;
@@ -492,12 +526,10 @@ class Closure {
     LC_TRY(split_gemm_tcgen05(g2, s_));
     ph_end(PH_GEMM2);
     gemm_launches_ += 2;
-    gemm_flops_ += 2.0 * 6.0 * (double)kb * (double)N_ * (double)P_;
-    const float es = (float)eta_screen_, ts = (float)tau_;
     ph_begin();
-    LC_TRY(screen_compact_f32(hn2f_, rn2f_, kb, es * es, ts * ts, idx_, stats_, s_));
+    LC_TRY(screen_compact_f32(hn2c_, rn2f_, kb, es * es, ts * ts, idx_, stats_, s_, nnz_, nz_idx_));
     ph_end(PH_SCREEN);
-    launches_ += 4;
+    launches_ += 6;
     return after_screen(t0);
   }
 

@@ -277,7 +277,9 @@ __global__ void k_gather_rows(const double* __restrict__ src, int lds, const int
 template <typename T>
 __global__ void __launch_bounds__(1024) k_screen_compact(const T* __restrict__ hn2, const T* __restrict__ rn2,
                                                          int count, T eta2, T tau2, int* __restrict__ idx,
-                                                         DevStats* stats) {
+                                                         DevStats* stats, const int* __restrict__ count_dev,
+                                                         const int* __restrict__ map) {
+  if (count_dev) count = min(count, *count_dev);
   __shared__ int wsum[32];
   __shared__ int base, nz_total;
   __shared__ double wmax[32];
@@ -311,7 +313,7 @@ __global__ void __launch_bounds__(1024) k_screen_compact(const T* __restrict__ h
     }
     __syncthreads();
     const int off = base + (w ? wsum[w - 1] : 0) + pre;
-    if (f) idx[off] = c;
+    if (f) idx[off] = map ? map[c] : c;
     __syncthreads();
     if (threadIdx.x == 0) base += wsum[31];
     __syncthreads();
@@ -465,13 +467,13 @@ cudaError_t gather_rows_f64(const double* src, int lds, const int* idx, int coun
 
 cudaError_t screen_compact_f64(const double* hn2, const double* rn2, int count, double eta2, double tau2, int* idx,
                                DevStats* stats, cudaStream_t s) {
-  k_screen_compact<double><<<1, 1024, 0, s>>>(hn2, rn2, count, eta2, tau2, idx, stats);
+  k_screen_compact<double><<<1, 1024, 0, s>>>(hn2, rn2, count, eta2, tau2, idx, stats, nullptr, nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t screen_compact_f32(const float* hn2, const float* rn2, int count, float eta2, float tau2, int* idx,
-                               DevStats* stats, cudaStream_t s) {
-  k_screen_compact<float><<<1, 1024, 0, s>>>(hn2, rn2, count, eta2, tau2, idx, stats);
+                               DevStats* stats, cudaStream_t s, const int* count_dev, const int* map) {
+  k_screen_compact<float><<<1, 1024, 0, s>>>(hn2, rn2, count, eta2, tau2, idx, stats, count_dev, map);
   return cudaGetLastError();
 }
 

@@ -85,8 +85,10 @@ cudaError_t gather_rows_f64(const double* src, int lds, const int* idx, int coun
 // candidate positions in order to idx and their count to stats->nflag
 cudaError_t screen_compact_f64(const double* hn2, const double* rn2, int count, double eta2,
                                double tau2, int* idx, DevStats* stats, cudaStream_t s);
+// count_dev (optional): live count on the device; map (optional): idx[i] = map[position]
 cudaError_t screen_compact_f32(const float* hn2, const float* rn2, int count, float eta2,
-                               float tau2, int* idx, DevStats* stats, cudaStream_t s);
+                               float tau2, int* idx, DevStats* stats, cudaStream_t s,
+                               const int* count_dev = nullptr, const int* map = nullptr);
 // sequential in-block accept for flagged row i (see lc_fp64.cu)
 cudaError_t accept_step(int i, int f, double* R, int ldr, double* rn2, const double* hn2,
                         double tol, double eta2, double* V, int ldv, int ncap, int P,
@@ -105,12 +107,28 @@ cudaError_t bracket_mixed(const double* V, int d, int ldv, long long t0, int cou
                           __nv_bfloat16* Hhi, __nv_bfloat16* Hlo, int ldh, float* hn2,
                           cudaStream_t s);
 
+// real 2d x 2d embeddings [[Hr, -Hi], [-Hi, -Hr]] of basis rows [r0, r1), split BF16
+cudaError_t build_embedding(const double* V, int ldv, int r0, int r1, int d, __nv_bfloat16* Ehi,
+                            __nv_bfloat16* Elo, cudaStream_t s);
+// ordered indices of the candidates with hn2 > eta2; their count to *nnz (device)
+cudaError_t compact_nonzero(const float* hn2, int count, float eta2, int* nz_idx, int* nnz, cudaStream_t s);
+// rows nz_idx[0 .. *nnz) of H (and their norms) -> consecutive rows of C
+cudaError_t gather_candidates(const __nv_bfloat16* Hhi, const __nv_bfloat16* Hlo, int ldh, const float* hn2,
+                              const int* nz_idx, const int* nnz, int count, int ncols, __nv_bfloat16* Chi,
+                              __nv_bfloat16* Clo, float* hn2c, cudaStream_t s);
+// tensor-core brackets (d = 64, 128) from the embeddings E (nelems elements)
+bool bracket_tc_supported(int d);
+cudaError_t bracket_tc(const __nv_bfloat16* Ehi, const __nv_bfloat16* Elo, long long nelems, int d, long long t0,
+                       int count, __nv_bfloat16* Hhi, __nv_bfloat16* Hlo, int ldh, float* hn2, long long spin_cap,
+                       DevStatus* st, cudaStream_t s);
+
 // tcgen05 split-BF16 GEMMs (lc_tcgen05.cu).  All operands K-major BF16.
 // D[M x N] = Ahi*Bhi^T + Ahi*Blo^T + Alo*Bhi^T with FP32 accumulation.
 struct SplitGemmArgs {
   const __nv_bfloat16 *Ahi, *Alo;  // M x K, row stride lda (elements)
   const __nv_bfloat16 *Bhi, *Blo;  // N x K, row stride ldb
   int M, N, K, lda, ldb;           // M % 128 == 0, N % BN == 0, K % 64 == 0
+  const int* Mdev;                 // optional device row count: CTAs at or past it exit
   // epilogue 0: store split BF16 of D to Dhi/Dlo (row stride ldd)
   __nv_bfloat16 *Dhi, *Dlo;
   int ldd;

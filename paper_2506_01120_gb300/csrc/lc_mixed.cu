@@ -166,3 +166,114 @@ cudaError_t bracket_mixed(const double* V, int d, int ldv, long long t0, int cou
 }
 
 }  // namespace lc
+
+// ------------------------------------------------ embeddings and compaction
+namespace lc {
+namespace {
+
+// E[i] = [[Hr, -Hi], [-Hi, -Hr]] (R x R, R = 2d, split BF16) for basis rows
+// i in [r0, r1), with H the Hermitian part of V[i] = iH unpacked from the
+// packed FP64 row.
+__global__ void k_build_embedding(const double* __restrict__ V, int ldv, int r0, int r1, int d,
+                                  __nv_bfloat16* __restrict__ Ehi, __nv_bfloat16* __restrict__ Elo) {
+  const int R = 2 * d;
+  const long long per = (long long)R * R;
+  const long long tot = per * (r1 - r0);
+  const double s1 = sqrt((double)d), s2 = sqrt((double)d / 2.0);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = r0 + e / per;
+    const int a = (int)((e / R) % R), b = (int)(e % R);
+    const int ja = a % d, jb = b % d;
+    const double* S = V + i * ldv;
+    double hr, hi;
+    if (ja == jb)      { hr = S[(long long)ja * d + ja] * s1; hi = 0.0; }
+    else if (ja < jb)  { hr = S[(long long)ja * d + jb] * s2; hi = S[(long long)jb * d + ja] * s2; }
+    else               { hr = S[(long long)jb * d + ja] * s2; hi = -S[(long long)ja * d + jb] * s2; }
+    const bool top = a < d, left = b < d;
+    const double v = (top && left) ? hr : ((top != left) ? -hi : -hr);
+    __nv_bfloat16 h, lo;
+    split_bf16(v, h, lo);
+    const long long o = (i * R + a) * R + b;
+    Ehi[o] = h;
+    Elo[o] = lo;
+  }
+}
+
+// ordered list of candidates with hn2 > eta2 (one CTA of 1024 threads)
+__global__ void __launch_bounds__(1024) k_compact_nonzero(const float* __restrict__ hn2, int count, float eta2,
+                                                          int* __restrict__ nz_idx, int* __restrict__ nnz) {
+  __shared__ int wsum[32];
+  __shared__ int base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c0 = 0; c0 < count; c0 += 1024) {
+    const int c = c0 + threadIdx.x;
+    const int f = (c < count && hn2[c] > eta2) ? 1 : 0;
+    const unsigned mask = __ballot_sync(0xffffffffu, f);
+    const int pre = __popc(mask & ((1u << lane) - 1u));
+    if (lane == 0) wsum[w] = __popc(mask);
+    __syncthreads();
+    if (w == 0) {
+      int v = wsum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
+      }
+      wsum[lane] = v;
+    }
+    __syncthreads();
+    if (f) nz_idx[base + (w ? wsum[w - 1] : 0) + pre] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) base += wsum[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *nnz = base;
+}
+
+// row i of the compacted block <- row nz_idx[i] (16-byte vectors)
+__global__ void k_gather_candidates(const __nv_bfloat16* __restrict__ Hhi, const __nv_bfloat16* __restrict__ Hlo,
+                                    int ldh, const float* __restrict__ hn2, const int* __restrict__ nz_idx,
+                                    const int* __restrict__ nnz, int ncols, __nv_bfloat16* __restrict__ Chi,
+                                    __nv_bfloat16* __restrict__ Clo, float* __restrict__ hn2c) {
+  const int i = blockIdx.x;
+  if (i >= *nnz) return;
+  const int src = nz_idx[i];
+  const uint4* sh = reinterpret_cast<const uint4*>(Hhi + (long long)src * ldh);
+  const uint4* sl = reinterpret_cast<const uint4*>(Hlo + (long long)src * ldh);
+  uint4* dh = reinterpret_cast<uint4*>(Chi + (long long)i * ldh);
+  uint4* dl = reinterpret_cast<uint4*>(Clo + (long long)i * ldh);
+  for (int v = threadIdx.x; v < ncols / 8; v += blockDim.x) {
+    dh[v] = sh[v];
+    dl[v] = sl[v];
+  }
+  if (threadIdx.x == 0) hn2c[i] = hn2[src];
+}
+
+}  // namespace
+
+cudaError_t build_embedding(const double* V, int ldv, int r0, int r1, int d, __nv_bfloat16* Ehi,
+                            __nv_bfloat16* Elo, cudaStream_t s) {
+  if (r1 <= r0) return cudaSuccess;
+  const long long tot = 4LL * d * d * (r1 - r0);
+  long long g = (tot + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_build_embedding<<<(int)g, 256, 0, s>>>(V, ldv, r0, r1, d, Ehi, Elo);
+  return cudaGetLastError();
+}
+
+cudaError_t compact_nonzero(const float* hn2, int count, float eta2, int* nz_idx, int* nnz, cudaStream_t s) {
+  k_compact_nonzero<<<1, 1024, 0, s>>>(hn2, count, eta2, nz_idx, nnz);
+  return cudaGetLastError();
+}
+
+cudaError_t gather_candidates(const __nv_bfloat16* Hhi, const __nv_bfloat16* Hlo, int ldh, const float* hn2,
+                              const int* nz_idx, const int* nnz, int count, int ncols, __nv_bfloat16* Chi,
+                              __nv_bfloat16* Clo, float* hn2c, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_gather_candidates<<<count, 256, 0, s>>>(Hhi, Hlo, ldh, hn2, nz_idx, nnz, ncols, Chi, Clo, hn2c);
+  return cudaGetLastError();
+}
+
+}  // namespace lc

@@ -148,6 +148,7 @@ __device__ void record_timeout(DevStatus* st, int where, long long info) {
 
 struct GemmParams {
   int M, N, K;
+  const int* Mdev;
   __nv_bfloat16 *Dhi, *Dlo;
   int ldd;
   const __nv_bfloat16 *Hhi, *Hlo;
@@ -173,6 +174,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
   const int nk = p.K / BK;
+  if (p.Mdev && m0 >= *p.Mdev) return;      // whole CTA: rows past the live count
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
 
   if (threadIdx.x == 0) {
@@ -383,6 +385,7 @@ cudaError_t split_gemm_tcgen05(const SplitGemmArgs& a, cudaStream_t s) {
   p.M = a.M;
   p.N = a.N;
   p.K = a.K;
+  p.Mdev = a.Mdev;
   p.Dhi = a.Dhi;
   p.Dlo = a.Dlo;
   p.ldd = a.ldd;
@@ -473,3 +476,193 @@ extern "C" LC_API int lc_split_gemm_f32(const float* A, const float* B, int M, i
   if (rc == LC_OK && hst.code != 0) rc = hst.code;
   return rc;
 }
+
+// ------------------------------------------------------- tensor-core brackets
+// One CTA per pair (l, m) of the block.  Each basis element v = iH is also
+// stored as its real 2d x 2d embedding E = [[Hr, -Hi], [-Hi, -Hr]] (split BF16,
+// row-major).  With A = H_l, B = H_m:
+//   E_l[0:d] E_m^T = [Re AB | Im AB],   E_m[0:d] E_l^T = [Re BA | Im BA]
+// (Hr symmetric, Hi antisymmetric), so one TMEM accumulator receives
+// D = [Re(AB - BA) | Im(AB - BA)] from 2 x 3 split MMAs per 16-wide k-step, the
+// second three with the negate-A bit of the instruction descriptor.  The
+// bracket [V_l, V_m] = -(AB - BA) has Hermitian part i(AB - BA), whose packed
+// row j is, from row j of D alone (AB - BA is anti-Hermitian, so Re is
+// antisymmetric):
+//   S[j][k] = -sqrt(2/d) Im D[j][k] (k > j),  -Im D[j][j]/sqrt(d) (k = j),
+//             -sqrt(2/d) Re D[j][k] (k < j).
+// The A operand is the first 128 rows of the same shared-memory tile (for
+// d = 64 rows 64..127 of D are unused).
+namespace lc {
+namespace {
+
+template <int D>
+struct BrCfg {
+  static constexpr int R = 2 * D;              // rows of E = MMA N = K extent
+  static constexpr int TILE = R * 64 * 2;       // one R x 64 BF16 tile
+  static constexpr int STAGE = 4 * TILE;        // El hi/lo, Em hi/lo
+  static constexpr int NK = R / 64;             // 64-wide k-chunks
+  static constexpr int SMEM = STAGE + 1024;
+  static constexpr int TMEM_COLS = R;
+};
+
+template <int D>
+__global__ void __launch_bounds__(128, 1)
+    k_bracket_tc(const __grid_constant__ CUtensorMap mEhi, const __grid_constant__ CUtensorMap mElo, long long t0,
+                 __nv_bfloat16* __restrict__ Hhi, __nv_bfloat16* __restrict__ Hlo, int ldh, float* __restrict__ hn2,
+                 uint64_t limit_ns, DevStatus* st) {
+  using C = BrCfg<D>;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar, empty_bar, done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  __shared__ float red[4];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pair = blockIdx.x;
+  int l, m;
+  pair_from_index(t0 + pair, &l, &m);
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  if (threadIdx.x == 0) {
+    mbar_init(&full_bar, 1);
+    mbar_init(&empty_bar, 1);
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    int issued = 0;
+    for (int kc = 0; kc < C::NK; ++kc) {
+      if (kc > 0 && !mbar_wait_bounded(&empty_bar, (uint32_t)(kc - 1) & 1u, limit_ns)) {
+        record_timeout(st, SITE_GEMM_TMA_WAIT, kc);
+        abort_flag = 1;
+        break;
+      }
+      if (*(volatile int*)&abort_flag) break;
+      mbar_expect_tx(&full_bar, C::STAGE);
+      const int x = kc * 64;
+      tma_load_2d(smem, &mEhi, &full_bar, x, l * C::R);
+      tma_load_2d(smem + C::TILE, &mElo, &full_bar, x, l * C::R);
+      tma_load_2d(smem + 2 * C::TILE, &mEhi, &full_bar, x, m * C::R);
+      tma_load_2d(smem + 3 * C::TILE, &mElo, &full_bar, x, m * C::R);
+      issued = kc + 1;
+    }
+    if (issued > 0) mbar_wait_bounded(&full_bar, (uint32_t)(issued - 1) & 1u, limit_ns);
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = make_idesc_bf16(128, C::R);
+    constexpr uint32_t idesc_neg = idesc | (1u << 13);      // negate A
+    for (int kc = 0; kc < C::NK; ++kc) {
+      if (!mbar_wait_bounded(&full_bar, (uint32_t)kc & 1u, limit_ns)) {
+        record_timeout(st, SITE_GEMM_MMA_WAIT, kc);
+        abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t lh = smem_u32(smem), ll = lh + C::TILE, mh = lh + 2 * C::TILE, ml = lh + 3 * C::TILE;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint32_t off = kk * 32;
+        const uint64_t dlh = make_sw128_desc(lh + off), dll = make_sw128_desc(ll + off);
+        const uint64_t dmh = make_sw128_desc(mh + off), dml = make_sw128_desc(ml + off);
+        mma_bf16(tmem, dlh, dmh, idesc, (kc | kk) ? 1u : 0u);
+        mma_bf16(tmem, dlh, dml, idesc, 1u);
+        mma_bf16(tmem, dll, dmh, idesc, 1u);
+        mma_bf16(tmem, dmh, dlh, idesc_neg, 1u);
+        mma_bf16(tmem, dmh, dll, idesc_neg, 1u);
+        mma_bf16(tmem, dml, dlh, idesc_neg, 1u);
+      }
+      mma_commit(&empty_bar);
+    }
+    mma_commit(&done_bar);
+  }
+  __syncwarp();
+  const bool have = mbar_wait_bounded(&done_bar, 0u, limit_ns);
+  if (!have) {
+    record_timeout(st, SITE_GEMM_EPI_WAIT, pair);
+    atomicExch(&abort_flag, 1);
+  }
+  __syncthreads();
+  tc_fence_after();
+  const bool run = !(*(volatile int*)&abort_flag);
+  const int j = warp * 32 + lane;                      // output row
+  float ss = 0.f;
+  if (run && warp * 32 < D) {                          // warp-uniform
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    const float s1 = rsqrtf((float)D), s2 = sqrtf(2.f / (float)D);
+    __nv_bfloat16* oh = Hhi + (long long)pair * ldh + (long long)j * D;
+    __nv_bfloat16* ol = Hlo + (long long)pair * ldh + (long long)j * D;
+    for (int c = 0; c < D; c += 32) {
+      float re[32], im[32];
+      tmem_ld_32cols(trow + (uint32_t)c, re);
+      tmem_ld_32cols(trow + (uint32_t)(D + c), im);
+      __align__(16) __nv_bfloat16 hi[32], lo[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int k = c + i;
+        const float v = (k > j) ? -s2 * im[i] : ((k == j) ? -s1 * im[i] : -s2 * re[i]);
+        ss = fmaf(v, v, ss);
+        hi[i] = __float2bfloat16_rn(v);
+        lo[i] = __float2bfloat16_rn(v - __bfloat162float(hi[i]));
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        reinterpret_cast<uint4*>(oh + c)[i] = reinterpret_cast<const uint4*>(hi)[i];
+        reinterpret_cast<uint4*>(ol + c)[i] = reinterpret_cast<const uint4*>(lo)[i];
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if (lane == 0) red[warp] = ss;
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && run) hn2[pair] = red[0] + red[1] + red[2] + red[3];
+  if (warp == 2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
+  }
+}
+
+template <int D>
+cudaError_t launch_bracket_tc(const __nv_bfloat16* Ehi, const __nv_bfloat16* Elo, long long nrows_elems,
+                              long long t0, int count, __nv_bfloat16* Hhi, __nv_bfloat16* Hlo, int ldh, float* hn2,
+                              long long spin_cap, DevStatus* st, cudaStream_t s) {
+  using C = BrCfg<D>;
+  CUtensorMap mh, ml;
+  if (!make_map(&mh, Ehi, nrows_elems * C::R, C::R, C::R, C::R) ||
+      !make_map(&ml, Elo, nrows_elems * C::R, C::R, C::R, C::R))
+    return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_bracket_tc<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const uint64_t lim = spin_cap > 0 ? (uint64_t)spin_cap : 4000000000ull;
+  k_bracket_tc<D><<<count, 128, C::SMEM, s>>>(mh, ml, t0, Hhi, Hlo, ldh, hn2, lim, st);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool bracket_tc_supported(int d) { return d == 64 || d == 128; }
+
+cudaError_t bracket_tc(const __nv_bfloat16* Ehi, const __nv_bfloat16* Elo, long long nelems, int d, long long t0,
+                       int count, __nv_bfloat16* Hhi, __nv_bfloat16* Hlo, int ldh, float* hn2, long long spin_cap,
+                       DevStatus* st, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (d == 64) return launch_bracket_tc<64>(Ehi, Elo, nelems, t0, count, Hhi, Hlo, ldh, hn2, spin_cap, st, s);
+  if (d == 128) return launch_bracket_tc<128>(Ehi, Elo, nelems, t0, count, Hhi, Hlo, ldh, hn2, spin_cap, st, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace lc

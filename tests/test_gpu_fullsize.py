@@ -81,3 +81,29 @@ def test_su128_random_growth_mixed():
     r = binding.lie_closure(g, 1e-8, precision="mixed", saturation_exit=1, return_basis=False)
     assert r.dim == 16383
     assert r.report["min_acc_rel_res"] > 1e-8
+
+
+def test_random_d64_mixed_matches_fp64_path():
+    """Random traceless pair at d = 64 (tensor-core brackets): the mixed path
+    accepts the same candidates as the FP64 path (itself pinned to the oracle
+    on small sizes), so the bases agree element by element."""
+    g = inputs.random_set(64, 2, seed=77)
+    a = binding.lie_closure(g, 1e-8, precision="mixed", saturation_exit=1)
+    b = binding.lie_closure(g, 1e-8, precision="fp64", saturation_exit=1)
+    assert a.dim == b.dim == 4095
+    assert oc.ortho_defect(a.basis[:512]) < 1e-12
+    np.testing.assert_allclose(a.basis, b.basis, atol=1e-10)
+    # the screen's noise floor stays far below its threshold
+    assert a.report["max_screen_rej_rel_res"] < 0.1 * a.report["tau_screen"]
+
+
+def test_su128_chain_growth_is_pauli():
+    """su(128) chain, stopped at saturation: dimension 4^7 - 1 and every sampled
+    element is +-i times a single Pauli string (brackets of strings are strings)."""
+    labels = inputs.su2n_chain_labels(7)
+    g = inputs.generators_from_labels(labels)
+    r = binding.lie_closure(g, 1e-8, precision="mixed", saturation_exit=1)
+    assert r.dim == 16383
+    rng = np.random.default_rng(3)
+    for i in rng.choice(r.dim, size=64, replace=False):
+        assert _pauli_label_of(r.basis[i], 7) is not None
