@@ -51,7 +51,9 @@ typedef enum {
   LC_ERR_CAPACITY = -4,          /* the basis would exceed max_dim; dim_out = max_dim */
   LC_ERR_CUDA = -5,              /* a CUDA runtime call failed */
   LC_ERR_OOM = -6,               /* device workspace could not be allocated */
-  LC_ERR_TIMEOUT = -7            /* a bounded device-side wait ran out */
+  LC_ERR_TIMEOUT = -7,           /* a bounded device-side wait ran out */
+  LC_ERR_TOO_LARGE = -8          /* problem exceeds a fixed-size buffer (see
+                                    lc_split_gemm_f32_noalloc) */
 } lc_status;
 
 typedef enum {

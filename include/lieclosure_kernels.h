@@ -30,6 +30,29 @@ extern "C" {
  */
 LC_API int lc_split_gemm_f32(const float* A, const float* B, int M, int N, int K, float* D, void* stream);
 
+/*
+ * lc_split_gemm_f32_noalloc -- lc_split_gemm_f32 without any device memory
+ * allocation.  The paper has no counterpart; this exists for callers that
+ * cannot let a library allocate: a process whose own pool already owns the
+ * free device memory, code under a hard memory cap, or a path where
+ * cudaMalloc/cudaFree (which may synchronise the device) is not allowed.
+ *
+ * Arguments, result and error codes are those of lc_split_gemm_f32.  The
+ * workspace is one fixed 32 MiB array in device global memory, created on
+ * every GPU that loads the library and kept until the process exits.  The
+ * padded problem must fit in it: 4 (Mp Kp + Np Kp) + 4 Mp Np bytes plus a
+ * little alignment, with Mp = M rounded up to 128, Np = N rounded up to 128
+ * and Kp = K rounded up to 64 (for example M = N = K = 1024 fits); larger
+ * problems return LC_ERR_TOO_LARGE without touching the GPU.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents; the
+ * call clears what must start at zero.  Calls that overlap on the GPU (for
+ * example on two streams at once) race on the array and give wrong results.
+ */
+LC_API int lc_split_gemm_f32_noalloc(const float* A, const float* B, int M, int N, int K, float* D,
+                                     void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,6 +24,7 @@ LC_ERR_CAPACITY = -4
 LC_ERR_CUDA = -5
 LC_ERR_OOM = -6
 LC_ERR_TIMEOUT = -7
+LC_ERR_TOO_LARGE = -8
 
 LC_PREC_FP64 = 0
 LC_PREC_MIXED_BF16X3 = 1
@@ -31,7 +32,7 @@ PRECISIONS = {"fp64": LC_PREC_FP64, "mixed": LC_PREC_MIXED_BF16X3}
 
 # every symbol the public headers declare
 EXPORTED = ["lc_default_options", "lc_status_string", "lc_version", "lie_closure", "lie_closure_dev",
-            "lie_closure_batched", "lc_split_gemm_f32"]
+            "lie_closure_batched", "lc_split_gemm_f32", "lc_split_gemm_f32_noalloc"]
 
 
 class LibraryNotBuilt(RuntimeError):
@@ -101,6 +102,8 @@ def lib():
         L.lie_closure_batched.restype = ctypes.c_int
         L.lc_split_gemm_f32.argtypes = [c_p, c_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_p, c_p]
         L.lc_split_gemm_f32.restype = ctypes.c_int
+        L.lc_split_gemm_f32_noalloc.argtypes = L.lc_split_gemm_f32.argtypes
+        L.lc_split_gemm_f32_noalloc.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -222,3 +225,25 @@ def lc_split_gemm_f32(A, B, stream=None):
     st = lib().lc_split_gemm_f32(A.data_ptr(), B.data_ptr(), M, N, K, D.data_ptr(), ctypes.c_void_p(s.cuda_stream))
     _check(st, True)
     return D
+
+
+def lc_split_gemm_f32_noalloc(A, B, stream=None, check: bool = True):
+    """D = A B^T like ``lc_split_gemm_f32``, with the library's fixed device
+    scratch array instead of a per-call allocation (for callers that cannot let
+    the library allocate).  Returns (D, status); D is allocated here by torch,
+    the library itself allocates nothing."""
+    import torch
+    if not (A.is_cuda and B.is_cuda and A.dtype == torch.float32 and B.dtype == torch.float32):
+        raise ValueError("A and B must be float32 CUDA tensors")
+    A = A.contiguous()
+    B = B.contiguous()
+    M, K = A.shape
+    N, K2 = B.shape
+    if K != K2:
+        raise ValueError("inner dimensions differ")
+    D = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = lib().lc_split_gemm_f32_noalloc(A.data_ptr(), B.data_ptr(), M, N, K, D.data_ptr(),
+                                         ctypes.c_void_p(s.cuda_stream))
+    _check(st, check)
+    return D, st

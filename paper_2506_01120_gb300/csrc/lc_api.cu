@@ -601,6 +601,7 @@ const char* lc_status_string(int s) {
     case LC_ERR_CUDA: return "CUDA error";
     case LC_ERR_OOM: return "out of device memory";
     case LC_ERR_TIMEOUT: return "device wait timed out";
+    case LC_ERR_TOO_LARGE: return "problem exceeds the fixed-size buffer";
     default: return "unknown status";
   }
 }

@@ -666,3 +666,91 @@ cudaError_t bracket_tc(const __nv_bfloat16* Ehi, const __nv_bfloat16* Elo, long 
 }
 
 }  // namespace lc
+
+// ------------------------------------------- allocation-free GEMM entry point
+// Some callers cannot let a library allocate device memory: a serving process
+// that hands all free device memory to its own pool at start-up, code running
+// under a hard memory cap, or a latency-critical path where cudaMalloc/cudaFree
+// (which can synchronise the whole device) must not appear.  For them,
+// lc_split_gemm_f32_noalloc runs the same split + tcgen05 GEMM + crop kernels
+// as lc_split_gemm_f32, but its workspace is this fixed file-scope device
+// array instead of a per-call allocation.  The array exists on every GPU that
+// loads the library and stays there until the process exits.
+namespace lc {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;   // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch, looked up once per device with that
+// device current.  (In host code the symbol itself is only a host-side
+// stand-in; kernels must be given this address.)
+cudaError_t noalloc_scratch_address(void** out) {
+  static std::mutex mu;
+  static void* addr[128] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    addr[dev] = p;
+  }
+  *out = addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace lc
+
+extern "C" LC_API int lc_split_gemm_f32_noalloc(const float* A, const float* B, int M, int N, int K, float* D,
+                                                void* stream) {
+  using namespace lc;
+  if (!A || !B || !D || M < 1 || N < 1 || K < 1) return LC_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t Mp = (size_t)round_up(M, BM), Np = (size_t)round_up(N, BN), Kp = (size_t)round_up(K, BK);
+  // layout inside the scratch array, every region 256-byte aligned
+  size_t off = 0;
+  auto place = [&](size_t bytes) { const size_t at = off; off = (off + bytes + 255) & ~size_t(255); return at; };
+  const size_t oAhi = place(Mp * Kp * 2), oAlo = place(Mp * Kp * 2);
+  const size_t oBhi = place(Np * Kp * 2), oBlo = place(Np * Kp * 2);
+  const size_t oD = place(Mp * Np * 4), oSt = place(sizeof(DevStatus));
+  if (off > kNoAllocScratchBytes) return LC_ERR_TOO_LARGE;
+  if (!tcgen05_available()) return LC_ERR_CUDA;
+  void* base = nullptr;
+  if (noalloc_scratch_address(&base) != cudaSuccess) return LC_ERR_CUDA;
+  char* ws = static_cast<char*>(base);
+  __nv_bfloat16* Ahi = reinterpret_cast<__nv_bfloat16*>(ws + oAhi);
+  __nv_bfloat16* Alo = reinterpret_cast<__nv_bfloat16*>(ws + oAlo);
+  __nv_bfloat16* Bhi = reinterpret_cast<__nv_bfloat16*>(ws + oBhi);
+  __nv_bfloat16* Blo = reinterpret_cast<__nv_bfloat16*>(ws + oBlo);
+  float* Dp = reinterpret_cast<float*>(ws + oD);
+  DevStatus* st = reinterpret_cast<DevStatus*>(ws + oSt);
+  int rc = LC_OK;
+  // the status word keeps the previous call's value: clear it.  The split
+  // buffers (padding included) and Dp are fully rewritten below.
+  if (cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess) rc = LC_ERR_CUDA;
+  if (rc == LC_OK) {
+    k_split_pad_f32<<<1024, 256, 0, s>>>(A, M, K, (int)Mp, (int)Kp, Ahi, Alo);
+    k_split_pad_f32<<<1024, 256, 0, s>>>(B, N, K, (int)Np, (int)Kp, Bhi, Blo);
+    SplitGemmArgs g;
+    memset(&g, 0, sizeof(g));
+    g.Ahi = Ahi; g.Alo = Alo; g.Bhi = Bhi; g.Blo = Blo;
+    g.M = (int)Mp; g.N = (int)Np; g.K = (int)Kp; g.lda = (int)Kp; g.ldb = (int)Kp;
+    g.Df32 = Dp; g.ldd = (int)Np; g.epilogue = 2; g.st = st;
+    if (split_gemm_tcgen05(g, s) != cudaSuccess) rc = LC_ERR_CUDA;
+  }
+  DevStatus hst;
+  memset(&hst, 0, sizeof(hst));
+  if (rc == LC_OK) {
+    k_crop_f32<<<1024, 256, 0, s>>>(Dp, (int)Np, M, N, D);
+    if (cudaGetLastError() != cudaSuccess) rc = LC_ERR_CUDA;
+    else if (cudaMemcpyAsync(&hst, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = LC_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess && rc == LC_OK) rc = LC_ERR_CUDA;
+  if (rc == LC_OK && hst.code != 0) rc = hst.code;
+  return rc;
+}
