@@ -109,7 +109,7 @@ class Closure {
     mixed_ = (o.precision == LC_PREC_MIXED_BF16X3);
     ldp_ = round_up(P_, 128);
     ncap_pad_ = (int)round_up_ll(ncap_, 128);
-    int K = o.block_k > 0 ? o.block_k : 2048;
+    int K = o.block_k > 0 ? o.block_k : (mixed_ ? 8192 : 2048);
     // bound the candidate buffers to about 3 GB
     const double per = mixed_ ? (8.0 * ldp_ + 4.0 * ldp_ + 4.0 * ncap_pad_ + 8.0 * ncap_)
                               : (24.0 * ldp_ + 8.0 * ncap_);
@@ -118,6 +118,7 @@ class Closure {
     K = std::max(K, k_);         // the generator pass is one block
     K_ = std::max(1, K);
     Kpad_ = round_up(K_, 128);
+    Kgrow_ = std::min(K_, 1024);
     tau_ = o.tau_screen > 0 ? o.tau_screen : 1e-3;
     eta_ = o.eta_abs > 0 ? o.eta_abs : 1e-12;
     eta_screen_ = std::max(eta_, 1e-5);
@@ -181,7 +182,7 @@ class Closure {
   }
 
  private:
-  int k_, d_, P_, ldp_, ncap_pad_, K_, Kpad_;
+  int k_, d_, P_, ldp_, ncap_pad_, K_, Kpad_, Kgrow_;
   double tol_, tau_, eta_, eta_screen_;
   long long ncap_;
   lc_options opt;
@@ -194,7 +195,10 @@ class Closure {
   // device buffers
   double *G64_ = nullptr, *V64_ = nullptr, *H64_ = nullptr, *S64_ = nullptr, *R64_ = nullptr, *beta64_ = nullptr;
   double *hn2_ = nullptr, *rn2_ = nullptr, *hnf_ = nullptr, *rnf_ = nullptr, *chk_ = nullptr;
-  int *idx_ = nullptr, *nonfinite_ = nullptr;
+  int *idx_ = nullptr, *nonfinite_ = nullptr, *need_ = nullptr;
+  unsigned int* bar_ = nullptr;
+  double* ws64_ = nullptr;
+  static constexpr size_t kWs64 = size_t(2) << 20;   // split-K workspace, doubles
   DevStats* stats_ = nullptr;
   DevStatus* st_ = nullptr;
   __nv_bfloat16 *Vhi_ = nullptr, *Vlo_ = nullptr, *VThi_ = nullptr, *VTlo_ = nullptr;
@@ -216,6 +220,9 @@ class Closure {
     st_ = ar_.take<DevStatus>(1);
     chk_ = ar_.take<double>(2);
     nonfinite_ = ar_.take<int>(1);
+    need_ = ar_.take<int>(1);
+    bar_ = ar_.take<unsigned int>(2);
+    ws64_ = ar_.take<double>(kWs64);
     if (!mixed_) {
       H64_ = ar_.take<double>((size_t)K_ * ldp_);
       S64_ = ar_.take<double>((size_t)K_ * ldp_);
@@ -284,6 +291,7 @@ class Closure {
       LC_TRY(cudaMemset2DAsync(V64_ + P_, sizeof(double) * ldp_, 0, sizeof(double) * (ldp_ - P_), ncap_, s_));
     }
     LC_TRY(cudaMemsetAsync(st_, 0, sizeof(DevStatus), s_));
+    LC_TRY(cudaMemsetAsync(bar_, 0, 2 * sizeof(unsigned int), s_));
     LC_TRY(cudaMemsetAsync(stats_, 0, sizeof(DevStats), s_));
     {
       // min_acc starts at +inf
@@ -377,25 +385,31 @@ class Closure {
     ev_pool_.clear();
   }
 
-  // Test-and-append of the f candidate rows in R64 (FP64, pair order).
+  // Test-and-append of the f candidate rows in R64 (FP64, pair order):
+  // classical Gram-Schmidt against the basis as it was when the block
+  // started (a second pass only when some row needs it), then the in-order
+  // test and append against that basis plus this block's accepts.
   int accept_rows(int f) {
     flagged_ += f;
     ph_begin();
     LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, hnf_, s_));
     const int n0 = (int)N_;
     if (n0 > 0) {
-      for (int pass = 0; pass < 2; ++pass) {
-        LC_TRY(gemm_nt_f64(f, n0, P_, R64_, ldp_, V64_, ldp_, beta64_, (int)ncap_, s_));
-        LC_TRY(gemm_nn_sub_f64(f, P_, n0, beta64_, (int)ncap_, V64_, ldp_, R64_, ldp_, s_));
-      }
-      launches_ += 4;
+      LC_TRY(gemm_nt_f64(f, n0, P_, R64_, ldp_, V64_, ldp_, beta64_, (int)ncap_, s_, ws64_, kWs64));
+      LC_TRY(gemm_nn_sub_f64(f, P_, n0, beta64_, (int)ncap_, V64_, ldp_, R64_, ldp_, s_, ws64_, kWs64));
+      LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, rnf_, s_));
+      LC_TRY(need_pass2(f, hnf_, rnf_, eta_ * eta_, tol_, need_, s_));
+      LC_TRY(gemm_nt_f64(f, n0, P_, R64_, ldp_, V64_, ldp_, beta64_, (int)ncap_, s_, ws64_, kWs64, need_));
+      LC_TRY(gemm_nn_sub_f64(f, P_, n0, beta64_, (int)ncap_, V64_, ldp_, R64_, ldp_, s_, ws64_, kWs64, need_));
+      LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, rnf_, s_, need_));
+      launches_ += 10;
+    } else {
+      LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, rnf_, s_));
     }
-    LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, rnf_, s_));
     LC_TRY(zero_stats(stats_, n0, s_));
-    for (int i = 0; i < f; ++i)
-      LC_TRY(accept_step(i, f, R64_, ldp_, rnf_, hnf_, tol_, eta_ * eta_, V64_, ldp_, (int)ncap_, P_, stats_, st_,
-                         nullptr, s_));
-    launches_ += 3 + f;
+    LC_TRY(accept_seq(f, R64_, ldp_, rnf_, hnf_, tol_, eta_ * eta_, V64_, ldp_, (int)ncap_, P_, stats_, st_, bar_,
+                      opt.spin_cap, s_));
+    launches_ += 4;
     ph_end(PH_ACCEPT);
     int rc = sync_read();
     const long long n1 = host_->stats.ncur;
@@ -446,12 +460,12 @@ class Closure {
     ph_end(PH_BRACKET);
     ph_begin();
     LC_TRY(rownorm2_f64(kb, P_, H64_, ldp_, hn2_, s_));
-    LC_TRY(gemm_nt_f64(kb, (int)N_, P_, H64_, ldp_, V64_, ldp_, beta64_, (int)ncap_, s_));
+    LC_TRY(gemm_nt_f64(kb, (int)N_, P_, H64_, ldp_, V64_, ldp_, beta64_, (int)ncap_, s_, ws64_, kWs64));
     ph_end(PH_GEMM1);
     ph_begin();
     LC_TRY(cudaMemcpy2DAsync(S64_, sizeof(double) * ldp_, H64_, sizeof(double) * ldp_, sizeof(double) * P_, kb,
                              cudaMemcpyDeviceToDevice, s_));
-    LC_TRY(gemm_nn_sub_f64(kb, P_, (int)N_, beta64_, (int)ncap_, V64_, ldp_, S64_, ldp_, s_));
+    LC_TRY(gemm_nn_sub_f64(kb, P_, (int)N_, beta64_, (int)ncap_, V64_, ldp_, S64_, ldp_, s_, ws64_, kWs64));
     LC_TRY(rownorm2_f64(kb, P_, S64_, ldp_, rn2_, s_));
     ph_end(PH_GEMM2);
     // one FP64 projection pass: ||r1|| <= tol/2 ||h|| implies the two-pass
@@ -533,17 +547,23 @@ class Closure {
     return after_screen(t0);
   }
 
+  // Block sizes: Kgrow_ while the basis grows (bounds the in-block sequential
+  // work and the duplicates screened in together), doubling up to K_ once a
+  // block appends nothing.  Any partition of the pair order gives the same
+  // result.
   int sweep() {
     t_ = 0;
+    long long knext = Kgrow_;
     for (;;) {
       const long long T = pairs_below(N_);
       if (t_ >= T) break;
       if (dmax_ >= 0 && N_ >= dmax_) break;
-      long long kb = std::min<long long>(K_, T - t_);
+      long long kb = std::min<long long>(std::min<long long>(knext, K_), T - t_);
       if (opt.max_candidates > 0) kb = std::min<long long>(kb, opt.max_candidates - checked_);
       if (kb <= 0) break;
       const long long n_before = N_;
       int rc = mixed_ ? block_mixed(t_, (int)kb) : block_fp64(t_, (int)kb);
+      knext = (N_ > n_before) ? Kgrow_ : std::min<long long>(2 * kb, K_);
       ++blocks_;
       t_ += kb;
       checked_ += kb;

@@ -6,6 +6,7 @@
 // (packing, gathers, the accept step's row updates).
 #include "lc_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 
 namespace lc {
@@ -177,61 +178,37 @@ __global__ void __launch_bounds__(256) k_bracket_f64(const double* __restrict__ 
 }
 
 // ------------------------------------------------------------ FP64 GEMMs
+// One templated tile kernel for C = A B^T (B stored N x K) and C = A B (B
+// stored K x N), 64 x 64 tiles, 4 x 4 outputs per thread.  blockIdx.z splits
+// K; with more than one split each CTA writes its partial tile to a workspace
+// and k_reduce_f64 adds the partials in a fixed order (deterministic).
+// mode: 0 store, 1 subtract from C, 2 partial to workspace.
 constexpr int GM = 64, GN = 64, GK = 16;
 
-// C[M x N] = A[M x K] * B[N x K]^T
-__global__ void __launch_bounds__(256) k_gemm_nt_f64(int M, int N, int K, const double* __restrict__ A, int lda,
-                                                     const double* __restrict__ B, int ldb,
-                                                     double* __restrict__ C, int ldc) {
+template <bool BT>
+__global__ void __launch_bounds__(256) k_gemm_f64(int M, int N, int K, int kchunk, const double* __restrict__ A,
+                                                  int lda, const double* __restrict__ B, int ldb,
+                                                  double* __restrict__ C, int ldc, int mode,
+                                                  double* __restrict__ ws, const int* __restrict__ run_if) {
+  if (run_if && *run_if == 0) return;
   __shared__ double sA[GK][GM + 2], sB[GK][GN + 2];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
+  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
   double acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += GK) {
-    for (int e = threadIdx.x; e < GM * GK; e += 256) {
-      const int r = e / GK, c = e % GK;
-      const int gm = m0 + r, gn = n0 + r, gk = k0 + c;
-      sA[c][r] = (gm < M && gk < K) ? A[(long long)gm * lda + gk] : 0.0;
-      sB[c][r] = (gn < N && gk < K) ? B[(long long)gn * ldb + gk] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < GK; ++q) {
-      double a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) { a[i] = sA[q][ty + 16 * i]; b[i] = sB[q][tx + 16 * i]; }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
-      if (gm < M && gn < N) C[(long long)gm * ldc + gn] = acc[i][j];
-    }
-}
-
-// C[M x N] -= A[M x K] * B[K x N]
-__global__ void __launch_bounds__(256) k_gemm_nn_sub_f64(int M, int N, int K, const double* __restrict__ A, int lda,
-                                                         const double* __restrict__ B, int ldb,
-                                                         double* __restrict__ C, int ldc) {
-  __shared__ double sA[GK][GM + 2], sB[GK][GN + 2];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
-  double acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += GK) {
+  for (int k0 = kb; k0 < ke; k0 += GK) {
     for (int e = threadIdx.x; e < GM * GK; e += 256) {
       const int r = e / GK, c = e % GK;
       const int gm = m0 + r, gk = k0 + c;
-      sA[c][r] = (gm < M && gk < K) ? A[(long long)gm * lda + gk] : 0.0;
-      const int rb = e / GN, cb = e % GN;       // B: row k0+rb, col n0+cb
-      const int bk = k0 + rb, bn = n0 + cb;
-      sB[rb][cb] = (bk < K && bn < N) ? B[(long long)bk * ldb + bn] : 0.0;
+      sA[c][r] = (gm < M && gk < ke) ? A[(long long)gm * lda + gk] : 0.0;
+      if (BT) {
+        const int gn = n0 + r;
+        sB[c][r] = (gn < N && gk < ke) ? B[(long long)gn * ldb + gk] : 0.0;
+      } else {
+        const int rb = e / GN, cb = e % GN;
+        const int bk = k0 + rb, bn = n0 + cb;
+        sB[rb][cb] = (bk < ke && bn < N) ? B[(long long)bk * ldb + bn] : 0.0;
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -251,11 +228,29 @@ __global__ void __launch_bounds__(256) k_gemm_nn_sub_f64(int M, int N, int K, co
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
-      if (gm < M && gn < N) C[(long long)gm * ldc + gn] -= acc[i][j];
+      if (gm >= M || gn >= N) continue;
+      if (mode == 0) C[(long long)gm * ldc + gn] = acc[i][j];
+      else if (mode == 1) C[(long long)gm * ldc + gn] -= acc[i][j];
+      else ws[((long long)blockIdx.z * M + gm) * N + gn] = acc[i][j];
     }
 }
 
-__global__ void k_rownorm2_f64(int M, int N, const double* __restrict__ A, int lda, double* __restrict__ out) {
+__global__ void k_reduce_f64(int M, int N, int S, const double* __restrict__ ws, double* __restrict__ C, int ldc,
+                             int subtract, const int* __restrict__ run_if) {
+  if (run_if && *run_if == 0) return;
+  const long long tot = (long long)M * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (int z = 0; z < S; ++z) t += ws[(long long)z * tot + e];
+    const long long o = (e / N) * ldc + (e % N);
+    if (subtract) C[o] -= t; else C[o] = t;
+  }
+}
+
+__global__ void k_rownorm2_f64(int M, int N, const double* __restrict__ A, int lda, double* __restrict__ out,
+                               const int* __restrict__ run_if) {
+  if (run_if && *run_if == 0) return;
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= M) return;
   const double* a = A + (long long)row * lda;
@@ -397,6 +392,123 @@ __global__ void __launch_bounds__(256) k_accept_step(int i, int f, double* __res
   if (threadIdx.x == 0) rn2[j] = s;
 }
 
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The
+// wait is bounded: after limit_ns the CTA records LC_ERR_TIMEOUT and returns
+// false, and the caller leaves the kernel.
+__device__ bool grid_barrier(unsigned int* count, unsigned int* gen, unsigned int nblocks, uint64_t limit_ns,
+                             DevStatus* st, int* ok_smem) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned int g0 = atomicAdd(gen, 0u);
+    __threadfence();
+    const unsigned int arrived = atomicAdd(count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      uint64_t t0;
+      asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t0));
+      for (unsigned int it = 0;; ++it) {
+        if (atomicAdd(gen, 0u) != g0) break;
+        if ((it & 63u) == 63u) {
+          uint64_t t;
+          asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+          if (t - t0 > limit_ns) {
+            if (atomicCAS(&st->code, 0, (int)LC_ERR_TIMEOUT) == 0) { st->where = SITE_ACCEPT_BARRIER; st->info = 0; }
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    __threadfence();
+    *ok_smem = ok;
+  }
+  __syncthreads();
+  return *ok_smem != 0;
+}
+
+// The whole in-block test-and-append of Algorithm 4 in one cooperative launch.
+// Rows R[0..f) are the flagged candidates in pair order, already
+// orthogonalised against the basis rows that existed when the block started;
+// rn2/hn2 hold squared residual and bracket norms.  For each i in order every
+// CTA takes the same decision (accept <=> ||h|| > eta_abs and ||r_i|| > tol
+// ||h||); on accept CTA 0 appends w = r_i / ||r_i|| to V and each CTA removes
+// the w component (twice) from the later rows it owns (row j belongs to CTA
+// j mod gridDim.x) and refreshes their norms; one grid barrier then publishes
+// the updated rows.  A rejected candidate changes nothing, so no barrier.
+__global__ void __launch_bounds__(256) k_accept_seq(int f, double* __restrict__ R, int ldr,
+                                                    double* __restrict__ rn2, const double* __restrict__ hn2,
+                                                    double tol, double eta2, double* __restrict__ V, int ldv,
+                                                    int ncap, int P, DevStats* stats, DevStatus* st,
+                                                    unsigned int* bar, uint64_t limit_ns) {
+  __shared__ double red[33];
+  __shared__ int slot, ok_smem;
+  const unsigned int G = gridDim.x;
+  for (int i = 0; i < f; ++i) {
+    const double h2 = hn2[i];
+    const double r2 = __ldcg(&rn2[i]);
+    const bool nonzero = h2 > eta2;
+    if (!(nonzero && r2 > tol * tol * h2)) {
+      if (blockIdx.x == 0 && threadIdx.x == 0 && nonzero) atomicMax(&stats->max_rej_bits, dbits(sqrt(r2 / h2)));
+      continue;
+    }
+    const double inv = 1.0 / sqrt(r2);
+    const double* ri = R + (long long)i * ldr;
+    if (blockIdx.x == 0) {
+      if (threadIdx.x == 0) {
+        int sl = stats->ncur;
+        if (sl >= ncap) {
+          if (atomicCAS(&st->code, 0, (int)LC_ERR_CAPACITY) == 0) { st->where = SITE_ACCEPT_CAPACITY; st->info = i; }
+          sl = -1;
+        } else {
+          stats->ncur = sl + 1;
+          stats->naccepted += 1;
+          atomicMin(&stats->min_acc_bits, dbits(sqrt(r2 / h2)));
+        }
+        slot = sl;
+      }
+      __syncthreads();
+      if (slot >= 0) {
+        double* v = V + (long long)slot * ldv;
+        for (int p = threadIdx.x; p < P; p += blockDim.x) v[p] = __ldcg(&ri[p]) * inv;
+      }
+    }
+    for (int j = i + 1 + (int)((blockIdx.x + G - (unsigned)((i + 1) % G)) % G); j < f; j += G) {
+      double* rj = R + (long long)j * ldr;
+      for (int pass = 0; pass < 2; ++pass) {
+        double sacc = 0.0;
+        for (int p = threadIdx.x; p < P; p += blockDim.x) sacc = fma(__ldcg(&ri[p]), rj[p], sacc);
+        const double c = block_sum(sacc, red) * inv * inv;
+        for (int p = threadIdx.x; p < P; p += blockDim.x) rj[p] = fma(-c, __ldcg(&ri[p]), rj[p]);
+      }
+      double sacc = 0.0;
+      for (int p = threadIdx.x; p < P; p += blockDim.x) sacc = fma(rj[p], rj[p], sacc);
+      sacc = block_sum(sacc, red);
+      if (threadIdx.x == 0) rn2[j] = sacc;
+    }
+    if (!grid_barrier(bar, bar + 1, G, limit_ns, st, &ok_smem)) return;
+  }
+}
+
+// Second Gram-Schmidt pass needed?  After one FP64 pass the loss of
+// orthogonality of r is about eps ||h|| / ||r||; when ||r|| >= ||h|| / sqrt(2)
+// for every row (or the row is certainly dependent, ||r|| <= tol ||h|| / 2)
+// one pass is already accurate to rounding (Daniel, Gragg, Kaufman and
+// Stewart's criterion).  Writes 1 to *need if any row needs the second pass.
+__global__ void k_need_pass2(int f, const double* __restrict__ hn2, const double* __restrict__ rn2, double eta2,
+                             double tol, int* need) {
+  int any = 0;
+  for (int i = threadIdx.x; i < f; i += blockDim.x) {
+    const double h2 = hn2[i], r2 = rn2[i];
+    if (h2 > eta2 && r2 < 0.5 * h2 && r2 > 0.25 * tol * tol * h2) any = 1;
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) *need = any;
+}
+
 __global__ void k_zero_stats(DevStats* stats, int ncur) {
   stats->ncur = ncur;
   stats->naccepted = 0;
@@ -435,25 +547,46 @@ cudaError_t bracket_fp64(const double* V, int d, int ldv, long long t0, const in
   return cudaGetLastError();
 }
 
-cudaError_t gemm_nt_f64(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
-                        int ldc, cudaStream_t s) {
-  if (M <= 0 || N <= 0) return cudaSuccess;
-  dim3 grid((N + GN - 1) / GN, (M + GM - 1) / GM);
-  k_gemm_nt_f64<<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc);
+namespace {
+// number of K splits so that a small output still spreads over the GPU; the
+// workspace holds S * M * N doubles
+int choose_splits(int M, int N, int K, size_t ws_doubles) {
+  const long long tiles = (long long)((M + GM - 1) / GM) * ((N + GN - 1) / GN);
+  int S = 1;
+  while (tiles * S < 2 * 152 && K / (2 * S) >= 256 && (size_t)(2 * S) * M * N <= ws_doubles) S *= 2;
+  return S;
+}
+
+template <bool BT>
+cudaError_t gemm_f64(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C, int ldc,
+                     bool subtract, double* ws, size_t ws_doubles, const int* run_if, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  const int S = ws ? choose_splits(M, N, K, ws_doubles) : 1;
+  const int kchunk = (K + S - 1) / S;
+  dim3 grid((N + GN - 1) / GN, (M + GM - 1) / GM, S);
+  if (S == 1) {
+    k_gemm_f64<BT><<<grid, 256, 0, s>>>(M, N, K, kchunk, A, lda, B, ldb, C, ldc, subtract ? 1 : 0, nullptr, run_if);
+    return cudaGetLastError();
+  }
+  k_gemm_f64<BT><<<grid, 256, 0, s>>>(M, N, K, kchunk, A, lda, B, ldb, C, ldc, 2, ws, run_if);
+  k_reduce_f64<<<grid_for((long long)M * N, 256), 256, 0, s>>>(M, N, S, ws, C, ldc, subtract ? 1 : 0, run_if);
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t gemm_nt_f64(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
+                        int ldc, cudaStream_t s, double* ws, size_t ws_doubles, const int* run_if) {
+  return gemm_f64<true>(M, N, K, A, lda, B, ldb, C, ldc, false, ws, ws_doubles, run_if, s);
 }
 
 cudaError_t gemm_nn_sub_f64(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
-                            int ldc, cudaStream_t s) {
-  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
-  dim3 grid((N + GN - 1) / GN, (M + GM - 1) / GM);
-  k_gemm_nn_sub_f64<<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc);
-  return cudaGetLastError();
+                            int ldc, cudaStream_t s, double* ws, size_t ws_doubles, const int* run_if) {
+  return gemm_f64<false>(M, N, K, A, lda, B, ldb, C, ldc, true, ws, ws_doubles, run_if, s);
 }
 
-cudaError_t rownorm2_f64(int M, int N, const double* A, int lda, double* out, cudaStream_t s) {
+cudaError_t rownorm2_f64(int M, int N, const double* A, int lda, double* out, cudaStream_t s, const int* run_if) {
   if (M <= 0) return cudaSuccess;
-  k_rownorm2_f64<<<(M + 7) / 8, 256, 0, s>>>(M, N, A, lda, out);
+  k_rownorm2_f64<<<(M + 7) / 8, 256, 0, s>>>(M, N, A, lda, out, run_if);
   return cudaGetLastError();
 }
 
@@ -481,6 +614,30 @@ cudaError_t accept_step(int i, int f, double* R, int ldr, double* rn2, const dou
                         double* V, int ldv, int ncap, int P, DevStats* stats, DevStatus* st, int* /*accepted_rows*/,
                         cudaStream_t s) {
   k_accept_step<<<f - i, 256, 0, s>>>(i, f, R, ldr, rn2, hn2, tol, eta2, V, ldv, ncap, P, stats, st);
+  return cudaGetLastError();
+}
+
+cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2, double tol, double eta2, double* V,
+                       int ldv, int ncap, int P, DevStats* stats, DevStatus* st, unsigned int* bar, long long spin_cap,
+                       cudaStream_t s) {
+  if (f <= 0) return cudaSuccess;
+  static int nblocks = 0;
+  if (nblocks == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_accept_seq, 256, 0);
+    nblocks = std::max(1, std::min(sms, sms * per));
+  }
+  const int G = std::max(1, std::min(nblocks, f));
+  uint64_t lim = spin_cap > 0 ? (uint64_t)spin_cap : 4000000000ull;
+  void* args[] = {&f, &R, &ldr, &rn2, (void*)&hn2, &tol, &eta2, &V, &ldv, &ncap, &P, &stats, &st, &bar, &lim};
+  return cudaLaunchCooperativeKernel((const void*)k_accept_seq, dim3(G), dim3(256), args, 0, s);
+}
+
+cudaError_t need_pass2(int f, const double* hn2, const double* rn2, double eta2, double tol, int* need,
+                       cudaStream_t s) {
+  k_need_pass2<<<1, 256, 0, s>>>(f, hn2, rn2, eta2, tol, need);
   return cudaGetLastError();
 }
 

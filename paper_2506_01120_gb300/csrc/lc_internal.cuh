@@ -35,6 +35,7 @@ enum : int {
   SITE_GEMM_TMA_WAIT = 2,
   SITE_GEMM_MMA_WAIT = 3,
   SITE_GEMM_EPI_WAIT = 4,
+  SITE_ACCEPT_BARRIER = 5,
 };
 
 // Accept-path statistics kept on the device (doubles stored by bit pattern so
@@ -73,12 +74,25 @@ cudaError_t unpack_basis(const double* V, int n, int d, int ldp, double2* out, c
 // given), packed into rows of out (row stride ldo)
 cudaError_t bracket_fp64(const double* V, int d, int ldv, long long t0, const int* idx,
                          int count, double* out, int ldo, cudaStream_t s);
-// C = A * B^T (BT) or C = C - A * B (!BT); row-major, FP64
+// C = A * B^T and C = C - A * B; row-major FP64.  ws (optional, ws_doubles
+// long) enables split-K for small outputs; run_if (optional, device): skip the
+// launch's work when *run_if == 0.
 cudaError_t gemm_nt_f64(int M, int N, int K, const double* A, int lda, const double* B, int ldb,
-                        double* C, int ldc, cudaStream_t s);
+                        double* C, int ldc, cudaStream_t s, double* ws = nullptr, size_t ws_doubles = 0,
+                        const int* run_if = nullptr);
 cudaError_t gemm_nn_sub_f64(int M, int N, int K, const double* A, int lda, const double* B,
-                            int ldb, double* C, int ldc, cudaStream_t s);
-cudaError_t rownorm2_f64(int M, int N, const double* A, int lda, double* out, cudaStream_t s);
+                            int ldb, double* C, int ldc, cudaStream_t s, double* ws = nullptr,
+                            size_t ws_doubles = 0, const int* run_if = nullptr);
+cudaError_t rownorm2_f64(int M, int N, const double* A, int lda, double* out, cudaStream_t s,
+                         const int* run_if = nullptr);
+// the in-block sequential test-and-append of f flagged rows, one cooperative
+// launch (bar: two zeroed unsigned ints)
+cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2, double tol, double eta2,
+                       double* V, int ldv, int ncap, int P, DevStats* stats, DevStatus* st,
+                       unsigned int* bar, long long spin_cap, cudaStream_t s);
+// *need = 1 iff some row needs a second Gram-Schmidt pass
+cudaError_t need_pass2(int f, const double* hn2, const double* rn2, double eta2, double tol, int* need,
+                       cudaStream_t s);
 cudaError_t gather_rows_f64(const double* src, int lds, const int* idx, int count, int ncols,
                             double* dst, int ldd, cudaStream_t s);
 // flags candidates with hn2 > eta^2 and rn2 > tau^2 hn2; writes the flagged
