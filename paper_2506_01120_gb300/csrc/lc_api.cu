@@ -13,11 +13,13 @@
 #include "lc_internal.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 using namespace lc;
@@ -122,7 +124,8 @@ class Closure {
     tau_ = o.tau_screen > 0 ? o.tau_screen : 1e-3;
     eta_ = o.eta_abs > 0 ? o.eta_abs : 1e-12;
     eta_screen_ = std::max(eta_, 1e-5);
-    tc_bracket_ = mixed_ && bracket_tc_supported(d);
+    big_bracket_ = mixed_ && !bracket_tc_supported(d) && bracket_big_supported(d);
+    tc_bracket_ = mixed_ && (bracket_tc_supported(d) || big_bracket_);
   }
 
   int run(const double2* d_gens, double2* d_basis_out, long long* dim_out, lc_report* rep) {
@@ -206,7 +209,7 @@ class Closure {
   __nv_bfloat16 *Chi_ = nullptr, *Clo_ = nullptr, *Ehi_ = nullptr, *Elo_ = nullptr;
   float *hn2f_ = nullptr, *rn2f_ = nullptr, *hn2c_ = nullptr;
   int *nz_idx_ = nullptr, *nnz_ = nullptr;
-  bool tc_bracket_ = false;
+  bool tc_bracket_ = false, big_bracket_ = false;
 
   void carve() {
     G64_ = ar_.take<double>((size_t)k_ * ldp_);
@@ -419,7 +422,7 @@ class Closure {
       LC_TRY(split_rows(V64_, ldp_, n0, (int)n1, P_, Vhi_, Vlo_, ldp_, VThi_, VTlo_, ncap_pad_, s_));
       launches_ += 1;
       if (tc_bracket_) {
-        LC_TRY(build_embedding(V64_, ldp_, n0, (int)n1, d_, Ehi_, Elo_, s_));
+        LC_TRY(build_embedding(V64_, ldp_, n0, (int)n1, d_, Ehi_, Elo_, s_, big_bracket_ ? 1 : 0));
         launches_ += 1;
       }
       ph_end(PH_OTHER);
@@ -480,7 +483,9 @@ class Closure {
 
   int block_mixed(long long t0, int kb) {
     ph_begin();
-    if (tc_bracket_) {
+    if (big_bracket_) {
+      LC_TRY(bracket_big(Ehi_, Elo_, ncap_, d_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, opt.spin_cap, st_, s_));
+    } else if (tc_bracket_) {
       LC_TRY(bracket_tc(Ehi_, Elo_, ncap_, d_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, opt.spin_cap, st_, s_));
     } else {
       LC_TRY(bracket_mixed(V64_, d_, ldp_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, s_));
@@ -593,6 +598,84 @@ int closure_device(const double2* d_gens, int k, int d, double tol, double2* d_b
   return rc;
 }
 
+// One closure from host buffers on stream s (generators copied in, basis
+// copied out), used by lie_closure and by each batched worker.
+int closure_host(const lc_c128* generators, int k, int d, double tol, lc_c128* basis_out, long long* dim_out,
+                 long long max_dim, const lc_options& o, lc_report* rep, cudaStream_t s) {
+  if (dim_out) *dim_out = 0;
+  int rc = check_args(generators, k, d, tol, max_dim, o);
+  if (rc != LC_OK) return rc;
+  const size_t gbytes = sizeof(double2) * (size_t)k * d * d;
+  const long long ncap = std::min<long long>(max_dim, (long long)d * d);
+  const size_t bbytes = basis_out ? sizeof(double2) * (size_t)ncap * d * d : 0;
+  double2 *dg = nullptr, *db = nullptr;
+  cudaMemPool_t pool;
+  if (get_pool(&pool) != cudaSuccess) rc = LC_ERR_CUDA;
+  if (rc == LC_OK && cudaMallocFromPoolAsync(reinterpret_cast<void**>(&dg), gbytes, pool, s) != cudaSuccess)
+    rc = LC_ERR_OOM;
+  if (rc == LC_OK && bbytes &&
+      cudaMallocFromPoolAsync(reinterpret_cast<void**>(&db), bbytes, pool, s) != cudaSuccess)
+    rc = LC_ERR_OOM;
+  if (rc == LC_OK && cudaMemcpyAsync(dg, generators, gbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    rc = LC_ERR_CUDA;
+  long long dim = 0;
+  if (rc == LC_OK) rc = closure_device(dg, k, d, tol, db, &dim, max_dim, o, rep, s);
+  if ((rc == LC_OK || rc == LC_ERR_CAPACITY) && db && dim > 0) {
+    if (cudaMemcpyAsync(basis_out, db, sizeof(double2) * (size_t)std::min(dim, ncap) * d * d,
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      rc = LC_ERR_CUDA;
+  }
+  if (dg) cudaFreeAsync(dg, s);
+  if (db) cudaFreeAsync(db, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && rc == LC_OK) rc = LC_ERR_CUDA;
+  if (dim_out) *dim_out = dim;
+  return rc;
+}
+
+// Independent sets: worker threads, one CUDA stream each, take sets in order
+// of decreasing size (d, then k) from a shared cursor, so the long closures
+// start first and the many small, latency-bound ones fill the gaps.
+int batched_host(int nsets, const lc_c128* const* generators, const int* k, const int* d, double tol,
+                 lc_c128* const* basis_out, const long long* max_dim, long long* dim_out, int* status_out,
+                 const lc_options& o, lc_report* rep) {
+  std::vector<int> order(nsets);
+  for (int i = 0; i < nsets; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    if (d[a] != d[b]) return d[a] > d[b];
+    return k[a] > k[b];
+  });
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LC_ERR_CUDA;
+  const int nworkers = std::max(1, std::min(nsets, 16));
+  std::atomic<int> next(0);
+  std::vector<int> status(nsets, LC_OK);
+  auto work = [&]() {
+    cudaSetDevice(dev);
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      for (int i = next.fetch_add(1); i < nsets; i = next.fetch_add(1)) status[order[i]] = LC_ERR_CUDA;
+      return;
+    }
+    for (int i = next.fetch_add(1); i < nsets; i = next.fetch_add(1)) {
+      const int q = order[i];
+      long long dim = 0;
+      status[q] = closure_host(generators[q], k[q], d[q], tol, basis_out ? basis_out[q] : nullptr, &dim,
+                               max_dim[q], o, rep ? rep + q : nullptr, s);
+      if (dim_out) dim_out[q] = dim;
+    }
+    cudaStreamDestroy(s);
+  };
+  std::vector<std::thread> pool;
+  for (int w = 0; w < nworkers; ++w) pool.emplace_back(work);
+  for (auto& t : pool) t.join();
+  int first = LC_OK;
+  for (int q = 0; q < nsets; ++q) {
+    if (status_out) status_out[q] = status[q];
+    if (status[q] != LC_OK && first == LC_OK) first = status[q];
+  }
+  return first;
+}
+
 }  // namespace
 
 extern "C" {
@@ -649,32 +732,8 @@ int lie_closure(const lc_c128* generators, int k, int d, double tol, lc_c128* ba
   if (rc != LC_OK) return rc;
   cudaStream_t s;
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return LC_ERR_CUDA;
-  const size_t gbytes = sizeof(double2) * (size_t)k * d * d;
-  const long long ncap = std::min<long long>(max_dim, (long long)d * d);
-  const size_t bbytes = basis_out ? sizeof(double2) * (size_t)ncap * d * d : 0;
-  double2 *dg = nullptr, *db = nullptr;
-  cudaMemPool_t pool;
-  rc = LC_OK;
-  if (get_pool(&pool) != cudaSuccess) rc = LC_ERR_CUDA;
-  if (rc == LC_OK && cudaMallocFromPoolAsync(reinterpret_cast<void**>(&dg), gbytes, pool, s) != cudaSuccess)
-    rc = LC_ERR_OOM;
-  if (rc == LC_OK && bbytes &&
-      cudaMallocFromPoolAsync(reinterpret_cast<void**>(&db), bbytes, pool, s) != cudaSuccess)
-    rc = LC_ERR_OOM;
-  if (rc == LC_OK && cudaMemcpyAsync(dg, generators, gbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
-    rc = LC_ERR_CUDA;
-  long long dim = 0;
-  if (rc == LC_OK) rc = closure_device(dg, k, d, tol, db, &dim, max_dim, o, rep, s);
-  if ((rc == LC_OK || rc == LC_ERR_CAPACITY) && db && dim > 0) {
-    if (cudaMemcpyAsync(basis_out, db, sizeof(double2) * (size_t)std::min(dim, ncap) * d * d,
-                        cudaMemcpyDeviceToHost, s) != cudaSuccess)
-      rc = LC_ERR_CUDA;
-  }
-  if (dg) cudaFreeAsync(dg, s);
-  if (db) cudaFreeAsync(db, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess && rc == LC_OK) rc = LC_ERR_CUDA;
+  rc = closure_host(generators, k, d, tol, basis_out, dim_out, max_dim, o, rep, s);
   cudaStreamDestroy(s);
-  if (dim_out) *dim_out = dim;
   return rc;
 }
 
@@ -682,16 +741,10 @@ int lie_closure_batched(int nsets, const lc_c128* const* generators, const int* 
                         lc_c128* const* basis_out, const long long* max_dim, long long* dim_out, int* status_out,
                         const lc_options* opt, lc_report* rep) {
   if (nsets < 0 || (nsets > 0 && (!generators || !k || !d || !max_dim))) return LC_ERR_ARG;
-  int first = LC_OK;
-  for (int s = 0; s < nsets; ++s) {
-    long long dim = 0;
-    int rc = lie_closure(generators[s], k[s], d[s], tol, basis_out ? basis_out[s] : nullptr, &dim, max_dim[s], opt,
-                         rep ? rep + s : nullptr);
-    if (dim_out) dim_out[s] = dim;
-    if (status_out) status_out[s] = rc;
-    if (rc != LC_OK && first == LC_OK) first = rc;
-  }
-  return first;
+  if (nsets == 0) return LC_OK;
+  lc_options o;
+  if (opt) o = *opt; else lc_default_options(&o);
+  return batched_host(nsets, generators, k, d, tol, basis_out, max_dim, dim_out, status_out, o, rep);
 }
 
 }  // extern "C"

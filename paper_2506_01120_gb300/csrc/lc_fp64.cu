@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 namespace lc {
 
@@ -183,29 +184,36 @@ __global__ void __launch_bounds__(256) k_bracket_f64(const double* __restrict__ 
 // K; with more than one split each CTA writes its partial tile to a workspace
 // and k_reduce_f64 adds the partials in a fixed order (deterministic).
 // mode: 0 store, 1 subtract from C, 2 partial to workspace.
-constexpr int GM = 64, GN = 64, GK = 16;
+constexpr int GK = 16;
 
-template <bool BT>
+// TM x TN output tile (TM * TN = 4096), 256 threads in a 16 x 16 layout, each
+// thread TM/16 rows x TN/16 columns.  TM = 16 for the skinny products of the
+// accept path (few flagged rows), TM = 64 otherwise.
+template <bool BT, int TM>
 __global__ void __launch_bounds__(256) k_gemm_f64(int M, int N, int K, int kchunk, const double* __restrict__ A,
                                                   int lda, const double* __restrict__ B, int ldb,
                                                   double* __restrict__ C, int ldc, int mode,
                                                   double* __restrict__ ws, const int* __restrict__ run_if) {
+  constexpr int TN = 4096 / TM, RI = TM / 16, RJ = TN / 16;
   if (run_if && *run_if == 0) return;
-  __shared__ double sA[GK][GM + 2], sB[GK][GN + 2];
+  __shared__ double sA[GK][TM + 2], sB[GK][TN + 2];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
   const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-  double acc[4][4] = {};
+  double acc[RI][RJ] = {};
   for (int k0 = kb; k0 < ke; k0 += GK) {
-    for (int e = threadIdx.x; e < GM * GK; e += 256) {
+    for (int e = threadIdx.x; e < TM * GK; e += 256) {
       const int r = e / GK, c = e % GK;
       const int gm = m0 + r, gk = k0 + c;
       sA[c][r] = (gm < M && gk < ke) ? A[(long long)gm * lda + gk] : 0.0;
+    }
+    for (int e = threadIdx.x; e < TN * GK; e += 256) {
       if (BT) {
-        const int gn = n0 + r;
+        const int r = e / GK, c = e % GK;
+        const int gn = n0 + r, gk = k0 + c;
         sB[c][r] = (gn < N && gk < ke) ? B[(long long)gn * ldb + gk] : 0.0;
       } else {
-        const int rb = e / GN, cb = e % GN;
+        const int rb = e / TN, cb = e % TN;
         const int bk = k0 + rb, bn = n0 + cb;
         sB[rb][cb] = (bk < ke && bn < N) ? B[(long long)bk * ldb + bn] : 0.0;
       }
@@ -213,20 +221,22 @@ __global__ void __launch_bounds__(256) k_gemm_f64(int M, int N, int K, int kchun
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < GK; ++q) {
-      double a[4], b[4];
+      double a[RI], b[RJ];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) { a[i] = sA[q][ty + 16 * i]; b[i] = sB[q][tx + 16 * i]; }
+      for (int i = 0; i < RI; ++i) a[i] = sA[q][ty + 16 * i];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < RJ; ++j) b[j] = sB[q][tx + 16 * j];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      for (int i = 0; i < RI; ++i)
+#pragma unroll
+        for (int j = 0; j < RJ; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < RI; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < RJ; ++j) {
       const int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
       if (gm >= M || gn >= N) continue;
       if (mode == 0) C[(long long)gm * ldc + gn] = acc[i][j];
@@ -548,29 +558,51 @@ cudaError_t bracket_fp64(const double* V, int d, int ldv, long long t0, const in
 }
 
 namespace {
-// number of K splits so that a small output still spreads over the GPU; the
-// workspace holds S * M * N doubles
-int choose_splits(int M, int N, int K, size_t ws_doubles) {
-  const long long tiles = (long long)((M + GM - 1) / GM) * ((N + GN - 1) / GN);
-  int S = 1;
-  while (tiles * S < 2 * 152 && K / (2 * S) >= 256 && (size_t)(2 * S) * M * N <= ws_doubles) S *= 2;
-  return S;
+// Number of K splits.  FP64 work per CTA is uniform, so the CTA count should
+// fill whole waves of the 152 SMs: S is the smallest split count giving at
+// least c * 152 CTAs for the smallest c >= 1 whose last wave is >= 85 % full,
+// subject to K / S >= 128 and the workspace holding S * M * N doubles.
+int choose_splits(int M, int N, int K, int TM, int TN, size_t ws_doubles) {
+  const long long tiles = (long long)((M + TM - 1) / TM) * ((N + TN - 1) / TN);
+  const int smax_k = std::max(1, K / 128);
+  const int smax_ws = (int)std::max<long long>(1, (long long)(ws_doubles / ((size_t)M * N)));
+  const int smax = std::min(smax_k, smax_ws);
+  if (tiles >= 4 * 152) return 1;
+  int best = 1;
+  double best_eff = 0.0;
+  for (int S = 1; S <= smax; ++S) {
+    const long long ctas = tiles * S;
+    const long long waves = (ctas + 151) / 152;
+    const double eff = (double)ctas / (double)(waves * 152);
+    if (eff > best_eff + 1e-9) { best_eff = eff; best = S; }
+    if (ctas >= 152 && eff >= 0.85) return S;
+  }
+  return best;
+}
+
+template <bool BT, int TM>
+cudaError_t gemm_f64_tm(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
+                        int ldc, bool subtract, double* ws, size_t ws_doubles, const int* run_if, cudaStream_t s) {
+  constexpr int TN = 4096 / TM;
+  const int S = ws ? choose_splits(M, N, K, TM, TN, ws_doubles) : 1;
+  const int kchunk = (K + S - 1) / S;
+  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, S);
+  if (S == 1) {
+    k_gemm_f64<BT, TM><<<grid, 256, 0, s>>>(M, N, K, kchunk, A, lda, B, ldb, C, ldc, subtract ? 1 : 0, nullptr,
+                                            run_if);
+    return cudaGetLastError();
+  }
+  k_gemm_f64<BT, TM><<<grid, 256, 0, s>>>(M, N, K, kchunk, A, lda, B, ldb, C, ldc, 2, ws, run_if);
+  k_reduce_f64<<<grid_for((long long)M * N, 256), 256, 0, s>>>(M, N, S, ws, C, ldc, subtract ? 1 : 0, run_if);
+  return cudaGetLastError();
 }
 
 template <bool BT>
 cudaError_t gemm_f64(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C, int ldc,
                      bool subtract, double* ws, size_t ws_doubles, const int* run_if, cudaStream_t s) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
-  const int S = ws ? choose_splits(M, N, K, ws_doubles) : 1;
-  const int kchunk = (K + S - 1) / S;
-  dim3 grid((N + GN - 1) / GN, (M + GM - 1) / GM, S);
-  if (S == 1) {
-    k_gemm_f64<BT><<<grid, 256, 0, s>>>(M, N, K, kchunk, A, lda, B, ldb, C, ldc, subtract ? 1 : 0, nullptr, run_if);
-    return cudaGetLastError();
-  }
-  k_gemm_f64<BT><<<grid, 256, 0, s>>>(M, N, K, kchunk, A, lda, B, ldb, C, ldc, 2, ws, run_if);
-  k_reduce_f64<<<grid_for((long long)M * N, 256), 256, 0, s>>>(M, N, S, ws, C, ldc, subtract ? 1 : 0, run_if);
-  return cudaGetLastError();
+  if (M < 128) return gemm_f64_tm<BT, 16>(M, N, K, A, lda, B, ldb, C, ldc, subtract, ws, ws_doubles, run_if, s);
+  return gemm_f64_tm<BT, 64>(M, N, K, A, lda, B, ldb, C, ldc, subtract, ws, ws_doubles, run_if, s);
 }
 }  // namespace
 
@@ -621,14 +653,15 @@ cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2
                        int ldv, int ncap, int P, DevStats* stats, DevStatus* st, unsigned int* bar, long long spin_cap,
                        cudaStream_t s) {
   if (f <= 0) return cudaSuccess;
-  static int nblocks = 0;
-  if (nblocks == 0) {
+  static std::once_flag once;
+  static int nblocks = 1;
+  std::call_once(once, [] {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_accept_seq, 256, 0);
     nblocks = std::max(1, std::min(sms, sms * per));
-  }
+  });
   const int G = std::max(1, std::min(nblocks, f));
   uint64_t lim = spin_cap > 0 ? (uint64_t)spin_cap : 4000000000ull;
   void* args[] = {&f, &R, &ldr, &rn2, (void*)&hn2, &tol, &eta2, &V, &ldv, &ncap, &P, &stats, &st, &bar, &lim};

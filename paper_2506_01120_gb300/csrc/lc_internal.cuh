@@ -122,8 +122,9 @@ cudaError_t bracket_mixed(const double* V, int d, int ldv, long long t0, int cou
                           cudaStream_t s);
 
 // real 2d x 2d embeddings [[Hr, -Hi], [-Hi, -Hr]] of basis rows [r0, r1), split BF16
+// (perm: rows in the large-d bracket order, see lc_tcgen05.cu)
 cudaError_t build_embedding(const double* V, int ldv, int r0, int r1, int d, __nv_bfloat16* Ehi,
-                            __nv_bfloat16* Elo, cudaStream_t s);
+                            __nv_bfloat16* Elo, cudaStream_t s, int perm = 0);
 // ordered indices of the candidates with hn2 > eta2; their count to *nnz (device)
 cudaError_t compact_nonzero(const float* hn2, int count, float eta2, int* nz_idx, int* nnz, cudaStream_t s);
 // rows nz_idx[0 .. *nnz) of H (and their norms) -> consecutive rows of C
@@ -135,6 +136,11 @@ bool bracket_tc_supported(int d);
 cudaError_t bracket_tc(const __nv_bfloat16* Ehi, const __nv_bfloat16* Elo, long long nelems, int d, long long t0,
                        int count, __nv_bfloat16* Hhi, __nv_bfloat16* Hlo, int ldh, float* hn2, long long spin_cap,
                        DevStatus* st, cudaStream_t s);
+// tensor-core brackets for d >= 256, d % 128 == 0, from the permuted embeddings
+bool bracket_big_supported(int d);
+cudaError_t bracket_big(const __nv_bfloat16* Ehi, const __nv_bfloat16* Elo, long long nelems, int d, long long t0,
+                        int count, __nv_bfloat16* Hhi, __nv_bfloat16* Hlo, int ldh, float* hn2, long long spin_cap,
+                        DevStatus* st, cudaStream_t s);
 
 // tcgen05 split-BF16 GEMMs (lc_tcgen05.cu).  All operands K-major BF16.
 // D[M x N] = Ahi*Bhi^T + Ahi*Blo^T + Alo*Bhi^T with FP32 accumulation.

@@ -174,7 +174,10 @@ namespace {
 // E[i] = [[Hr, -Hi], [-Hi, -Hr]] (R x R, R = 2d, split BF16) for basis rows
 // i in [r0, r1), with H the Hermitian part of V[i] = iH unpacked from the
 // packed FP64 row.
-__global__ void k_build_embedding(const double* __restrict__ V, int ldv, int r0, int r1, int d,
+// With perm != 0 the rows are stored in the order used by the large-d
+// bracket kernel: stored row 128c + w holds E row 64c + w (w < 64) and stored
+// row 128c + 64 + w holds E row d + 64c + w.
+__global__ void k_build_embedding(const double* __restrict__ V, int ldv, int r0, int r1, int d, int perm,
                                   __nv_bfloat16* __restrict__ Ehi, __nv_bfloat16* __restrict__ Elo) {
   const int R = 2 * d;
   const long long per = (long long)R * R;
@@ -183,7 +186,8 @@ __global__ void k_build_embedding(const double* __restrict__ V, int ldv, int r0,
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
     const long long i = r0 + e / per;
-    const int a = (int)((e / R) % R), b = (int)(e % R);
+    const int r = (int)((e / R) % R), b = (int)(e % R);
+    const int a = perm ? (((r & 127) < 64) ? 64 * (r >> 7) + (r & 127) : d + 64 * (r >> 7) + (r & 127) - 64) : r;
     const int ja = a % d, jb = b % d;
     const double* S = V + i * ldv;
     double hr, hi;
@@ -194,7 +198,7 @@ __global__ void k_build_embedding(const double* __restrict__ V, int ldv, int r0,
     const double v = (top && left) ? hr : ((top != left) ? -hi : -hr);
     __nv_bfloat16 h, lo;
     split_bf16(v, h, lo);
-    const long long o = (i * R + a) * R + b;
+    const long long o = (i * R + r) * R + b;
     Ehi[o] = h;
     Elo[o] = lo;
   }
@@ -254,12 +258,12 @@ __global__ void k_gather_candidates(const __nv_bfloat16* __restrict__ Hhi, const
 }  // namespace
 
 cudaError_t build_embedding(const double* V, int ldv, int r0, int r1, int d, __nv_bfloat16* Ehi,
-                            __nv_bfloat16* Elo, cudaStream_t s) {
+                            __nv_bfloat16* Elo, cudaStream_t s, int perm) {
   if (r1 <= r0) return cudaSuccess;
   const long long tot = 4LL * d * d * (r1 - r0);
   long long g = (tot + 255) / 256;
   if (g > 152 * 32) g = 152 * 32;
-  k_build_embedding<<<(int)g, 256, 0, s>>>(V, ldv, r0, r1, d, Ehi, Elo);
+  k_build_embedding<<<(int)g, 256, 0, s>>>(V, ldv, r0, r1, d, perm, Ehi, Elo);
   return cudaGetLastError();
 }
 

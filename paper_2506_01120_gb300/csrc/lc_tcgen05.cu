@@ -172,7 +172,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+  // Grouped tile order: consecutive CTAs sweep all N tiles of a group of
+  // GROUP_M row tiles, so one wave touches a few M tiles and a few N tiles
+  // and both operands are reused from L2 instead of re-read from DRAM.
+  constexpr int GROUP_M = 8;
+  const int ntn = p.N / BN, ntm = p.M / BM;
+  const int id = blockIdx.x;
+  const int per_group = GROUP_M * ntn;
+  const int g = id / per_group, first_m = g * GROUP_M;
+  const int gm = min(GROUP_M, ntm - first_m);
+  const int in_g = id - g * per_group;
+  const int m0 = (first_m + in_g % gm) * BM, n0 = (in_g / gm) * BN;
   const int nk = p.K / BK;
   if (p.Mdev && m0 >= *p.Mdev) return;      // whole CTA: rows past the live count
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -262,7 +272,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   // ---------------- epilogue: all four warps
   const bool have = mbar_wait_bounded(&done_bar, 0u, p.limit_ns);
   if (!have) {
-    record_timeout(p.st, SITE_GEMM_EPI_WAIT, blockIdx.y * gridDim.x + blockIdx.x);
+    record_timeout(p.st, SITE_GEMM_EPI_WAIT, blockIdx.x);
     atomicExch(&abort_flag, 1);
   }
   __syncthreads();                   // makes the run decision uniform across the CTA
@@ -375,12 +385,12 @@ cudaError_t split_gemm_tcgen05(const SplitGemmArgs& a, cudaStream_t s) {
   if (!make_map(&mAhi, a.Ahi, a.M, a.K, a.lda, BM) || !make_map(&mAlo, a.Alo, a.M, a.K, a.lda, BM) ||
       !make_map(&mBhi, a.Bhi, a.N, a.K, a.ldb, BN) || !make_map(&mBlo, a.Blo, a.N, a.K, a.ldb, BN))
     return cudaErrorInvalidValue;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_split_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(k_split_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
   GemmParams p;
   p.M = a.M;
   p.N = a.N;
@@ -397,8 +407,8 @@ cudaError_t split_gemm_tcgen05(const SplitGemmArgs& a, cudaStream_t s) {
   p.epilogue = a.epilogue;
   p.limit_ns = a.spin_cap > 0 ? (uint64_t)a.spin_cap : 4000000000ull;
   p.st = a.st;
-  dim3 grid(a.N / BN, a.M / BM);
-  k_split_gemm<<<grid, NTHREADS, SMEM_BYTES, s>>>(mAhi, mAlo, mBhi, mBlo, p);
+  const int ntiles = (a.N / BN) * (a.M / BM);
+  k_split_gemm<<<ntiles, NTHREADS, SMEM_BYTES, s>>>(mAhi, mAlo, mBhi, mBlo, p);
   return cudaGetLastError();
 }
 
@@ -641,12 +651,12 @@ cudaError_t launch_bracket_tc(const __nv_bfloat16* Ehi, const __nv_bfloat16* Elo
   if (!make_map(&mh, Ehi, nrows_elems * C::R, C::R, C::R, C::R) ||
       !make_map(&ml, Elo, nrows_elems * C::R, C::R, C::R, C::R))
     return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_bracket_tc<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(k_bracket_tc<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
   const uint64_t lim = spin_cap > 0 ? (uint64_t)spin_cap : 4000000000ull;
   k_bracket_tc<D><<<count, 128, C::SMEM, s>>>(mh, ml, t0, Hhi, Hlo, ldh, hn2, lim, st);
   return cudaGetLastError();
@@ -754,3 +764,196 @@ extern "C" LC_API int lc_split_gemm_f32_noalloc(const float* A, const float* B, 
   if (rc == LC_OK && hst.code != 0) rc = hst.code;
   return rc;
 }
+
+// --------------------------------------------------- large-d tensor brackets
+// For d >= 256 (d % 128 == 0) a bracket is a d x 2d x 2d real GEMM per term.
+// The embedding is stored with its rows permuted in groups of 64:
+//   E'[128c + w] = E[64c + w] (w < 64),  E'[128c + 64 + w] = E[d + 64c + w],
+// so the 128-row N tile c of E' produces [Re | Im] of output columns
+// 64c .. 64c+63, and the A operand (the first d rows of E) is E' rows
+// 128c .. 128c+63 for c = 0 .. d/64-1 (two 64-row boxes per 128-row M tile).
+// One CTA per (pair, M tile, N tile): K runs over 2d columns twice, first
+// E_l[top] E'_m^T, then -E_m[top] E'_l^T, into one TMEM accumulator; the
+// epilogue writes the packed slots of rows m0..m0+127, columns 64c..64c+63, as
+// the small-d kernel does, and adds the row sums of squares to hn2[pair].
+namespace lc {
+namespace {
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_bracket_big(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+                  const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, int d,
+                  long long t0, __nv_bfloat16* __restrict__ Hhi, __nv_bfloat16* __restrict__ Hlo, int ldh,
+                  float* __restrict__ hn2, uint64_t limit_ns, DevStatus* st) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  __shared__ float red[4];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int R = 2 * d;
+  const int ntm = d / BM, ntn = R / BN, tpp = ntm * ntn;
+  const int pair = blockIdx.x / tpp, tile = blockIdx.x % tpp;
+  const int tm = tile / ntn, tn = tile % ntn;
+  int l, m;
+  pair_from_index(t0 + pair, &l, &m);
+  const int nkseg = R / BK, nk = 2 * nkseg;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    int issued = 0;
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+      if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1u, limit_ns)) {
+        record_timeout(st, SITE_GEMM_TMA_WAIT, kt);
+        abort_flag = 1;
+        break;
+      }
+      if (*(volatile int*)&abort_flag) break;
+      const bool second = kt >= nkseg;
+      const int a_elem = second ? m : l, b_elem = second ? l : m;
+      const int kx = (kt % nkseg) * BK;
+      uint8_t* sp = smem + s * STAGE_BYTES;
+      mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+      const int arow = a_elem * R + 256 * tm;           // two 64-row boxes: +0 and +128
+      tma_load_2d(sp, &mAhi, &full_bar[s], kx, arow);
+      tma_load_2d(sp + TILE_A_BYTES / 2, &mAhi, &full_bar[s], kx, arow + 128);
+      tma_load_2d(sp + TILE_A_BYTES, &mAlo, &full_bar[s], kx, arow);
+      tma_load_2d(sp + TILE_A_BYTES + TILE_A_BYTES / 2, &mAlo, &full_bar[s], kx, arow + 128);
+      const int brow = b_elem * R + BN * tn;
+      tma_load_2d(sp + 2 * TILE_A_BYTES, &mBhi, &full_bar[s], kx, brow);
+      tma_load_2d(sp + 2 * TILE_A_BYTES + TILE_B_BYTES, &mBlo, &full_bar[s], kx, brow);
+      issued = kt + 1;
+    }
+    for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt)
+      mbar_wait_bounded(&full_bar[kt % STAGES], (uint32_t)(kt / STAGES) & 1u, limit_ns);
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = make_idesc_bf16(BM, BN);
+    constexpr uint32_t idesc_neg = idesc | (1u << 13);
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+      if (!mbar_wait_bounded(&full_bar[s], ph, limit_ns)) {
+        record_timeout(st, SITE_GEMM_MMA_WAIT, kt);
+        abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t id = kt >= nkseg ? idesc_neg : idesc;
+      const uint32_t a_hi = smem_u32(smem + s * STAGE_BYTES);
+      const uint32_t a_lo = a_hi + TILE_A_BYTES;
+      const uint32_t b_hi = a_hi + 2 * TILE_A_BYTES;
+      const uint32_t b_lo = b_hi + TILE_B_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint32_t off = kk * 32;
+        const uint64_t dAh = make_sw128_desc(a_hi + off), dAl = make_sw128_desc(a_lo + off);
+        const uint64_t dBh = make_sw128_desc(b_hi + off), dBl = make_sw128_desc(b_lo + off);
+        mma_bf16(tmem, dAh, dBh, id, (kt | kk) ? 1u : 0u);
+        mma_bf16(tmem, dAh, dBl, id, 1u);
+        mma_bf16(tmem, dAl, dBh, id, 1u);
+      }
+      mma_commit(&empty_bar[s]);
+    }
+    mma_commit(&done_bar);
+  }
+  __syncwarp();
+  const bool have = mbar_wait_bounded(&done_bar, 0u, limit_ns);
+  if (!have) {
+    record_timeout(st, SITE_GEMM_EPI_WAIT, blockIdx.x);
+    atomicExch(&abort_flag, 1);
+  }
+  __syncthreads();
+  tc_fence_after();
+  const bool run = !(*(volatile int*)&abort_flag);
+  const int j = tm * BM + warp * 32 + lane;           // output row
+  const int kbase = 64 * tn;                          // output columns kbase .. kbase+63
+  float ss = 0.f;
+  if (run) {
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    const float s1 = rsqrtf((float)d), s2 = sqrtf(2.f / (float)d);
+    __nv_bfloat16* oh = Hhi + (long long)pair * ldh + (long long)j * d + kbase;
+    __nv_bfloat16* ol = Hlo + (long long)pair * ldh + (long long)j * d + kbase;
+    for (int c = 0; c < 64; c += 32) {
+      float re[32], im[32];
+      tmem_ld_32cols(trow + (uint32_t)c, re);
+      tmem_ld_32cols(trow + (uint32_t)(64 + c), im);
+      __align__(16) __nv_bfloat16 hi[32], lo[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int k = kbase + c + i;
+        const float v = (k > j) ? -s2 * im[i] : ((k == j) ? -s1 * im[i] : -s2 * re[i]);
+        ss = fmaf(v, v, ss);
+        hi[i] = __float2bfloat16_rn(v);
+        lo[i] = __float2bfloat16_rn(v - __bfloat162float(hi[i]));
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        reinterpret_cast<uint4*>(oh + c)[i] = reinterpret_cast<const uint4*>(hi)[i];
+        reinterpret_cast<uint4*>(ol + c)[i] = reinterpret_cast<const uint4*>(lo)[i];
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if (lane == 0) red[warp] = ss;
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && run) atomicAdd(&hn2[pair], red[0] + red[1] + red[2] + red[3]);
+  if (warp == 2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+}  // namespace
+
+bool bracket_big_supported(int d) { return d >= 256 && d % 128 == 0; }
+
+cudaError_t bracket_big(const __nv_bfloat16* Ehi, const __nv_bfloat16* Elo, long long nelems, int d, long long t0,
+                        int count, __nv_bfloat16* Hhi, __nv_bfloat16* Hlo, int ldh, float* hn2, long long spin_cap,
+                        DevStatus* st, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (!bracket_big_supported(d)) return cudaErrorInvalidValue;
+  const long long R = 2LL * d;
+  CUtensorMap ah, al, bh, bl;
+  if (!make_map(&ah, Ehi, nelems * R, R, R, 64) || !make_map(&al, Elo, nelems * R, R, R, 64) ||
+      !make_map(&bh, Ehi, nelems * R, R, R, BN) || !make_map(&bl, Elo, nelems * R, R, R, BN))
+    return cudaErrorInvalidValue;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(k_bracket_big, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  cudaError_t e = cudaMemsetAsync(hn2, 0, sizeof(float) * count, s);
+  if (e != cudaSuccess) return e;
+  const long long tpp = (long long)(d / BM) * (2 * d / BN);
+  const uint64_t lim = spin_cap > 0 ? (uint64_t)spin_cap : 4000000000ull;
+  k_bracket_big<<<(unsigned)(tpp * count), NTHREADS, SMEM_BYTES, s>>>(ah, al, bh, bl, d, t0, Hhi, Hlo, ldh, hn2, lim,
+                                                                     st);
+  return cudaGetLastError();
+}
+
+}  // namespace lc

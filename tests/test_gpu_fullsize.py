@@ -107,3 +107,41 @@ def test_su128_chain_growth_is_pauli():
     rng = np.random.default_rng(3)
     for i in rng.choice(r.dim, size=64, replace=False):
         assert _pauli_label_of(r.basis[i], 7) is not None
+
+
+def test_so16_chain_d256_large_bracket_matches_fp64():
+    """d = 256 goes through the large-d tensor-core bracket kernel; the mixed
+    basis equals the FP64 path's element by element, and its dimension is
+    n(2n-1) = 120 (so(16)), the exact Pauli closure's count."""
+    labels = inputs.so2n_chain_labels(8)
+    g = inputs.generators_from_labels(labels)
+    a = binding.lie_closure(g, 1e-8, max_dim=160, precision="mixed")
+    b = binding.lie_closure(g, 1e-8, max_dim=160, precision="fp64")
+    assert a.dim == b.dim == 120 == len(oc.pauli_closure(labels))
+    np.testing.assert_allclose(a.basis, b.basis, atol=1e-10)
+
+
+def test_so20_chain_d1024_full():
+    """The d = 1024 open chain closes to so(20): dimension 190, every element
+    +-i times one of the exact closure's Pauli strings."""
+    g, labels = inputs.workload_generators("so20_chain_d1024")
+    r = binding.lie_closure(g, 1e-8, max_dim=256, precision="mixed")
+    want = set(oc.pauli_closure(labels))
+    assert r.dim == 190 == len(want)
+    assert r.report["brackets_checked"] == 190 * 189 // 2
+    rng = np.random.default_rng(5)
+    for i in rng.choice(r.dim, size=12, replace=False):
+        assert _pauli_label_of(r.basis[i], 10) in want
+
+
+def test_batched256_per_set_dims():
+    """The 256-set batched workload (saturation exit on): random traceless sets
+    reach su(d), Pauli sets reach exactly their string closure."""
+    sets = inputs.batched_sets(256, seed=1120)
+    dims, stat, _, reps = binding.lie_closure_batched([s["generators"] for s in sets], 1e-8, saturation_exit=1)
+    assert all(st == 0 for st in stat)
+    for s, dim in zip(sets, dims):
+        if s["kind"] == "pauli":
+            assert dim == len(oc.pauli_closure(s["labels"])), s["labels"]
+        else:
+            assert dim == s["d"] ** 2 - 1
