@@ -49,6 +49,8 @@ def parse():
                     help="candidates of the FP64 GPU comparison run (0 = skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample budget (0 = skip)")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--ref-seconds", type=float, default=0.0,
+                    help="reference arm: oracle seconds per step (0 = about a minute in total)")
     return ap.parse_args()
 
 
@@ -175,7 +177,8 @@ def oracle_sample(seconds: float):
 def run_reference(args, world, rank, pg):
     if rank != 0:
         return
-    per_step = max(2.0, min(15.0, 60.0 / max(1, args.steps + args.warmup)))
+    per_step = args.ref_seconds if args.ref_seconds > 0 else \
+        max(2.0, min(15.0, 60.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         oracle_sample(per_step / 4)
     rates, walls, cores, cands = [], [], 1, 0
