@@ -84,6 +84,11 @@ typedef struct {
   int verbose;                /* nonzero: per-block log lines on stderr */
   int profile;                /* nonzero: time each phase with CUDA events on
                                  the call's stream (lc_report.t_phase_s) */
+  int fault_inject;           /* test hook, 0 in normal use: nonzero makes the
+                                 first grid barrier of the in-block accept wait
+                                 for an arrival that never comes, so its bounded
+                                 wait runs out (spin_cap) and the call returns
+                                 LC_ERR_TIMEOUT with the device still usable */
 } lc_options;
 
 typedef struct {

@@ -48,7 +48,8 @@ class LieClosureError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("eta_abs", ctypes.c_double), ("tau_screen", ctypes.c_double),
                 ("block_k", ctypes.c_int), ("saturation_exit", ctypes.c_int), ("spin_cap", ctypes.c_longlong),
-                ("max_candidates", ctypes.c_longlong), ("verbose", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("max_candidates", ctypes.c_longlong), ("verbose", ctypes.c_int), ("profile", ctypes.c_int),
+                ("fault_inject", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):

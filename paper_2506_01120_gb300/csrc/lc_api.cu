@@ -411,7 +411,7 @@ class Closure {
     }
     LC_TRY(zero_stats(stats_, n0, s_));
     LC_TRY(accept_seq(f, R64_, ldp_, rnf_, hnf_, tol_, eta_ * eta_, V64_, ldp_, (int)ncap_, P_, stats_, st_, bar_,
-                      opt.spin_cap, s_));
+                      opt.spin_cap, s_, opt.fault_inject ? 1 : 0));
     launches_ += 4;
     ph_end(PH_ACCEPT);
     int rc = sync_read();
@@ -692,6 +692,7 @@ void lc_default_options(lc_options* o) {
   o->max_candidates = 0;
   o->verbose = 0;
   o->profile = 0;
+  o->fault_inject = 0;
 }
 
 const char* lc_status_string(int s) {

@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(256) k_accept_seq(int f, double* __restrict__ 
                                                     double* __restrict__ rn2, const double* __restrict__ hn2,
                                                     double tol, double eta2, double* __restrict__ V, int ldv,
                                                     int ncap, int P, DevStats* stats, DevStatus* st,
-                                                    unsigned int* bar, uint64_t limit_ns) {
+                                                    unsigned int* bar, uint64_t limit_ns, int phantom) {
   __shared__ double red[33];
   __shared__ int slot, ok_smem;
   const unsigned int G = gridDim.x;
@@ -499,7 +499,8 @@ __global__ void __launch_bounds__(256) k_accept_seq(int f, double* __restrict__ 
       sacc = block_sum(sacc, red);
       if (threadIdx.x == 0) rn2[j] = sacc;
     }
-    if (!grid_barrier(bar, bar + 1, G, limit_ns, st, &ok_smem)) return;
+    // phantom (test hook): one more arrival is expected than there are CTAs
+    if (!grid_barrier(bar, bar + 1, G + (unsigned)phantom, limit_ns, st, &ok_smem)) return;
   }
 }
 
@@ -651,7 +652,7 @@ cudaError_t accept_step(int i, int f, double* R, int ldr, double* rn2, const dou
 
 cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2, double tol, double eta2, double* V,
                        int ldv, int ncap, int P, DevStats* stats, DevStatus* st, unsigned int* bar, long long spin_cap,
-                       cudaStream_t s) {
+                       cudaStream_t s, int phantom) {
   if (f <= 0) return cudaSuccess;
   static std::once_flag once;
   static int nblocks = 1;
@@ -664,7 +665,7 @@ cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2
   });
   const int G = std::max(1, std::min(nblocks, f));
   uint64_t lim = spin_cap > 0 ? (uint64_t)spin_cap : 4000000000ull;
-  void* args[] = {&f, &R, &ldr, &rn2, (void*)&hn2, &tol, &eta2, &V, &ldv, &ncap, &P, &stats, &st, &bar, &lim};
+  void* args[] = {&f, &R, &ldr, &rn2, (void*)&hn2, &tol, &eta2, &V, &ldv, &ncap, &P, &stats, &st, &bar, &lim, &phantom};
   return cudaLaunchCooperativeKernel((const void*)k_accept_seq, dim3(G), dim3(256), args, 0, s);
 }
 

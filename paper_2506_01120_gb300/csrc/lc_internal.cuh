@@ -89,7 +89,7 @@ cudaError_t rownorm2_f64(int M, int N, const double* A, int lda, double* out, cu
 // launch (bar: two zeroed unsigned ints)
 cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2, double tol, double eta2,
                        double* V, int ldv, int ncap, int P, DevStats* stats, DevStatus* st,
-                       unsigned int* bar, long long spin_cap, cudaStream_t s);
+                       unsigned int* bar, long long spin_cap, cudaStream_t s, int phantom = 0);
 // *need = 1 iff some row needs a second Gram-Schmidt pass
 cudaError_t need_pass2(int f, const double* hn2, const double* rn2, double eta2, double tol, int* need,
                        cudaStream_t s);

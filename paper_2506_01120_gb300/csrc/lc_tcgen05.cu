@@ -19,6 +19,7 @@
 #include "../../include/lieclosure_kernels.h"
 
 #include <cuda.h>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -35,6 +36,9 @@ constexpr int STAGE_BYTES = 2 * TILE_A_BYTES + 2 * TILE_B_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;   // + alignment slack
 constexpr int TMEM_COLS = BN;                // FP32 accumulator columns
 constexpr int NTHREADS = 128;
+// Limit for the waits that only let already-issued copies and MMAs land before
+// a CTA leaves (kept independent of the caller's progress-wait limit).
+constexpr uint64_t kDrainNs = 2000000000ull;
 
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -233,7 +237,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // is still writing shared memory when the CTA exits
     for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt) {
       const int s = kt % STAGES;
-      mbar_wait_bounded(&full_bar[s], (uint32_t)(kt / STAGES) & 1u, p.limit_ns);
+      mbar_wait_bounded(&full_bar[s], (uint32_t)(kt / STAGES) & 1u, kDrainNs);
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
@@ -274,6 +278,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (!have) {
     record_timeout(p.st, SITE_GEMM_EPI_WAIT, blockIdx.x);
     atomicExch(&abort_flag, 1);
+    mbar_wait_bounded(&done_bar, 0u, kDrainNs);      // issued MMAs retire before TMEM is freed
   }
   __syncthreads();                   // makes the run decision uniform across the CTA
   tc_fence_after();
@@ -567,7 +572,7 @@ __global__ void __launch_bounds__(128, 1)
       tma_load_2d(smem + 3 * C::TILE, &mElo, &full_bar, x, m * C::R);
       issued = kc + 1;
     }
-    if (issued > 0) mbar_wait_bounded(&full_bar, (uint32_t)(issued - 1) & 1u, limit_ns);
+    if (issued > 0) mbar_wait_bounded(&full_bar, (uint32_t)(issued - 1) & 1u, kDrainNs);
   } else if (warp == 1 && lane == 0) {
     constexpr uint32_t idesc = make_idesc_bf16(128, C::R);
     constexpr uint32_t idesc_neg = idesc | (1u << 13);      // negate A
@@ -600,6 +605,7 @@ __global__ void __launch_bounds__(128, 1)
   if (!have) {
     record_timeout(st, SITE_GEMM_EPI_WAIT, pair);
     atomicExch(&abort_flag, 1);
+    mbar_wait_bounded(&done_bar, 0u, kDrainNs);
   }
   __syncthreads();
   tc_fence_after();
@@ -848,7 +854,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       issued = kt + 1;
     }
     for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt)
-      mbar_wait_bounded(&full_bar[kt % STAGES], (uint32_t)(kt / STAGES) & 1u, limit_ns);
+      mbar_wait_bounded(&full_bar[kt % STAGES], (uint32_t)(kt / STAGES) & 1u, kDrainNs);
   } else if (warp == 1 && lane == 0) {
     constexpr uint32_t idesc = make_idesc_bf16(BM, BN);
     constexpr uint32_t idesc_neg = idesc | (1u << 13);
@@ -884,6 +890,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (!have) {
     record_timeout(st, SITE_GEMM_EPI_WAIT, blockIdx.x);
     atomicExch(&abort_flag, 1);
+    mbar_wait_bounded(&done_bar, 0u, kDrainNs);
   }
   __syncthreads();
   tc_fence_after();

@@ -52,7 +52,7 @@ def test_host_only_calls(built_lib):
 
 def test_struct_layouts_match_header():
     """ctypes mirrors of lc_options / lc_report have the C sizes."""
-    assert ctypes.sizeof(binding.Options) == 4 + 4 + 8 + 8 + 4 + 4 + 8 + 8 + 4 + 4
+    assert ctypes.sizeof(binding.Options) == 4 + 4 + 8 + 8 + 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4
     assert ctypes.sizeof(binding.Report) == 8 * 8 + 8 * 5 + 8 + 8 + 8 + 8 + 8 * 6 + 4 * 2
 
 

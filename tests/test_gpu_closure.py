@@ -199,3 +199,17 @@ def test_batched_small_sets():
             ref = oc.alg4_orthonormalization(s["generators"], 1e-8, saturation_exit=True)
             assert dim == ref.dim
             assert oc.span_distance(B, ref.basis) < 1e-6
+
+
+# ------------------------------------------------------------ failure detection
+def test_forced_wait_timeout_is_reported_and_device_stays_usable():
+    """The accept kernel's grid barrier is told to expect one arrival more than
+    there are CTAs (a flag nothing sets); its bounded wait runs out after
+    spin_cap ns, the kernel records LC_ERR_TIMEOUT and returns, and the next
+    call on the same device works."""
+    g = inputs.generators_from_labels(inputs.su2n_chain_labels(3))
+    for prec in PRECS:
+        r = binding.lie_closure(g, 1e-10, precision=prec, fault_inject=1, spin_cap=50_000_000, check=False)
+        assert r.status == binding.LC_ERR_TIMEOUT
+        ok = binding.lie_closure(g, 1e-10, precision=prec)
+        assert ok.status == binding.LC_OK and ok.dim == 63
