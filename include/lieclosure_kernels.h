@@ -41,8 +41,8 @@ LC_API int lc_split_gemm_f32(const float* A, const float* B, int M, int N, int K
  * workspace is one fixed 32 MiB array in device global memory, created on
  * every GPU that loads the library and kept until the process exits.  The
  * padded problem must fit in it: 4 (Mp Kp + Np Kp) + 4 Mp Np bytes plus a
- * little alignment, with Mp = M rounded up to 128, Np = N rounded up to 128
- * and Kp = K rounded up to 64 (for example M = N = K = 1024 fits); larger
+ * little alignment, with Mp = M rounded up to 128, Np = N rounded up to 256
+ * and Kp = K rounded up to 32 (for example M = N = K = 1024 fits); larger
  * problems return LC_ERR_TOO_LARGE without touching the GPU.
  * The first call on a device looks up the array's device address with that
  * device current; make that first call before any stream capture.

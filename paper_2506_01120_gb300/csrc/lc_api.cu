@@ -109,13 +109,15 @@ class Closure {
       : k_(k), d_(d), tol_(tol), ncap_(ncap), opt(o), s_(s) {
     P_ = d * d;
     mixed_ = (o.precision == LC_PREC_MIXED_BF16X3);
-    ldp_ = round_up(P_, 128);
-    ncap_pad_ = (int)round_up_ll(ncap_, 128);
-    int K = o.block_k > 0 ? o.block_k : (mixed_ ? 8192 : 2048);
-    // bound the candidate buffers to about 3 GB
+    // pad to the screening GEMM's N tile (it runs over both the basis and the
+    // packed components as its N extent)
+    ldp_ = round_up(P_, std::max(128, split_gemm_tile_n()));
+    ncap_pad_ = (int)round_up_ll(ncap_, std::max(128, split_gemm_tile_n()));
+    int K = o.block_k > 0 ? o.block_k : (mixed_ ? 16384 : 2048);
+    // bound the candidate buffers to about 8 GB
     const double per = mixed_ ? (8.0 * ldp_ + 4.0 * ldp_ + 4.0 * ncap_pad_ + 8.0 * ncap_)
                               : (24.0 * ldp_ + 8.0 * ncap_);
-    const int kmem = (int)std::max(1.0, std::min(1.0e9, 3.0e9 / per));
+    const int kmem = (int)std::max(1.0, std::min(1.0e9, 8.0e9 / per));
     K = std::min(K, kmem);
     K = std::max(K, k_);         // the generator pass is one block
     K_ = std::max(1, K);
@@ -499,7 +501,7 @@ class Closure {
     LC_TRY(gather_candidates(Hhi_, Hlo_, ldp_, hn2f_, nz_idx_, nnz_, kb, ldp_, Chi_, Clo_, hn2c_, s_));
     ph_end(PH_SCREEN);
     const int M = round_up(kb, 128);
-    const int Npad = round_up((int)N_, 128);
+    const int Npad = round_up((int)N_, std::max(128, split_gemm_tile_n()));
     SplitGemmArgs g1;
     memset(&g1, 0, sizeof(g1));
     g1.Ahi = Chi_;
@@ -710,7 +712,7 @@ const char* lc_status_string(int s) {
   }
 }
 
-const char* lc_version(void) { return "lieclosure-gb300 0.1 (sm_103a)"; }
+const char* lc_version(void) { return "lieclosure-gb300 0.3 (sm_103a; screening GEMM 128x256x32)"; }
 
 int lie_closure_dev(const lc_c128* generators, int k, int d, double tol, lc_c128* basis_out, long long* dim_out,
                     long long max_dim, const lc_options* opt, lc_report* rep, void* stream) {

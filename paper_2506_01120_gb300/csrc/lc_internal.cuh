@@ -147,7 +147,7 @@ cudaError_t bracket_big(const __nv_bfloat16* Ehi, const __nv_bfloat16* Elo, long
 struct SplitGemmArgs {
   const __nv_bfloat16 *Ahi, *Alo;  // M x K, row stride lda (elements)
   const __nv_bfloat16 *Bhi, *Blo;  // N x K, row stride ldb
-  int M, N, K, lda, ldb;           // M % 128 == 0, N % BN == 0, K % 64 == 0
+  int M, N, K, lda, ldb;           // M % 128, N % split_gemm_tile_n(), K % split_gemm_tile_k() == 0
   const int* Mdev;                 // optional device row count: CTAs at or past it exit
   // epilogue 0: store split BF16 of D to Dhi/Dlo (row stride ldd)
   __nv_bfloat16 *Dhi, *Dlo;
@@ -162,6 +162,10 @@ struct SplitGemmArgs {
   DevStatus* st;
 };
 cudaError_t split_gemm_tcgen05(const SplitGemmArgs& a, cudaStream_t s);
+// tile extents of split_gemm_tcgen05: N must be a multiple of split_gemm_tile_n(),
+// K of split_gemm_tile_k(), M of 128
+int split_gemm_tile_n();
+int split_gemm_tile_k();
 bool tcgen05_available();
 
 }  // namespace lc

@@ -106,6 +106,24 @@ __device__ __forceinline__ uint64_t make_sw128_desc(uint32_t saddr) {
   return desc;
 }
 
+// The same for rows of 64 bytes (32 BF16) with 64-byte swizzle: 8-row groups
+// 512 bytes apart, layout type 4.
+__device__ __forceinline__ uint64_t make_sw64_desc(uint32_t saddr) {
+  uint64_t desc = 0;
+  desc |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  desc |= (uint64_t)1u << 16;
+  desc |= (uint64_t)(512u >> 4) << 32;
+  desc |= (uint64_t)1u << 46;
+  desc |= (uint64_t)4u << 61;                  // SWIZZLE_64B
+  return desc;
+}
+
+template <int SWB>
+__device__ __forceinline__ uint64_t make_sw_desc(uint32_t saddr) {
+  static_assert(SWB == 64 || SWB == 128, "swizzle");
+  return SWB == 128 ? make_sw128_desc(saddr) : make_sw64_desc(saddr);
+}
+
 // Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and B
 // BF16 (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22,
 // M >> 4 at bits 24-28.
@@ -150,6 +168,21 @@ __device__ void record_timeout(DevStatus* st, int where, long long info) {
   }
 }
 
+// Tile configuration of the screening GEMM: 128 x BN output tile, BK-wide
+// k-slices (BK BF16 = one swizzle row of 2 BK bytes), ST pipeline stages.
+template <int BN_, int BK_, int ST_>
+struct GemmCfg {
+  static constexpr int BN = BN_, BK = BK_, STAGES = ST_;
+  static constexpr int SWB = 2 * BK_;                 // swizzle width in bytes
+  static constexpr int TILE_A = BM * BK_ * 2, TILE_B = BN_ * BK_ * 2;
+  static constexpr int STAGE = 2 * TILE_A + 2 * TILE_B;
+  static constexpr int SMEM = ST_ * STAGE + 1024;
+  static constexpr int TMEM_COLS = BN_;
+};
+// 128 x 256 tiles with 32-wide k-slices: 25 % fewer operand bytes per MMA
+// flop than 128 x 128, and 4 x 48 KB stages in flight.
+using ScreenCfg = GemmCfg<256, 32, 4>;
+
 struct GemmParams {
   int M, N, K;
   const int* Mdev;
@@ -164,11 +197,15 @@ struct GemmParams {
   DevStatus* st;
 };
 
+template <class G>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_split_gemm(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                  const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
                  const GemmParams p) {
   extern __shared__ uint8_t smem_raw[];
+  constexpr int BN = G::BN, BK = G::BK, STAGES = G::STAGES;
+  constexpr int TILE_A_BYTES = G::TILE_A, TILE_B_BYTES = G::TILE_B, STAGE_BYTES = G::STAGE;
+  constexpr int TMEM_COLS = G::TMEM_COLS;
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
   __shared__ __align__(8) uint64_t done_bar;
@@ -260,8 +297,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
         const uint32_t off = kk * 32;   // 16 BF16 along K inside the swizzled row
-        const uint64_t dAh = make_sw128_desc(a_hi + off), dAl = make_sw128_desc(a_lo + off);
-        const uint64_t dBh = make_sw128_desc(b_hi + off), dBl = make_sw128_desc(b_lo + off);
+        const uint64_t dAh = make_sw_desc<G::SWB>(a_hi + off), dAl = make_sw_desc<G::SWB>(a_lo + off);
+        const uint64_t dBh = make_sw_desc<G::SWB>(b_hi + off), dBl = make_sw_desc<G::SWB>(b_lo + off);
         mma_bf16(tmem, dAh, dBh, idesc, (kt | kk) ? 1u : 0u);
         mma_bf16(tmem, dAh, dBl, idesc, 1u);
         mma_bf16(tmem, dAl, dBh, idesc, 1u);
@@ -359,16 +396,18 @@ EncodeTiledFn get_encode() {
 // 2-D BF16 map: rows x cols (cols contiguous, row stride ld elements),
 // box = box_rows x 64 with 128-byte swizzle.
 bool make_map(CUtensorMap* m, const __nv_bfloat16* base, long long rows, long long cols, long long ld,
-              int box_rows) {
+              int box_rows, int box_cols = BK) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapSwizzle sw = box_cols == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  if (box_cols != 64 && box_cols != 32) return false;
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides, box,
-                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
@@ -383,17 +422,18 @@ bool tcgen05_available() {
 }
 
 cudaError_t split_gemm_tcgen05(const SplitGemmArgs& a, cudaStream_t s) {
+  using G = ScreenCfg;
   if (a.M <= 0 || a.N <= 0) return cudaSuccess;
-  if (a.M % BM || a.N % BN || a.K % BK || a.K <= 0) return cudaErrorInvalidValue;
-  if ((a.lda % 64) || (a.ldb % 64)) return cudaErrorInvalidValue;
+  if (a.M % BM || a.N % G::BN || a.K % G::BK || a.K <= 0) return cudaErrorInvalidValue;
+  if ((a.lda % 8) || (a.ldb % 8)) return cudaErrorInvalidValue;   // TMA: 16-byte row strides
   CUtensorMap mAhi, mAlo, mBhi, mBlo;
-  if (!make_map(&mAhi, a.Ahi, a.M, a.K, a.lda, BM) || !make_map(&mAlo, a.Alo, a.M, a.K, a.lda, BM) ||
-      !make_map(&mBhi, a.Bhi, a.N, a.K, a.ldb, BN) || !make_map(&mBlo, a.Blo, a.N, a.K, a.ldb, BN))
+  if (!make_map(&mAhi, a.Ahi, a.M, a.K, a.lda, BM, G::BK) || !make_map(&mAlo, a.Alo, a.M, a.K, a.lda, BM, G::BK) ||
+      !make_map(&mBhi, a.Bhi, a.N, a.K, a.ldb, G::BN, G::BK) || !make_map(&mBlo, a.Blo, a.N, a.K, a.ldb, G::BN, G::BK))
     return cudaErrorInvalidValue;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_split_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    attr_err = cudaFuncSetAttribute(k_split_gemm<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
   });
   if (attr_err != cudaSuccess) return attr_err;
   GemmParams p;
@@ -412,10 +452,13 @@ cudaError_t split_gemm_tcgen05(const SplitGemmArgs& a, cudaStream_t s) {
   p.epilogue = a.epilogue;
   p.limit_ns = a.spin_cap > 0 ? (uint64_t)a.spin_cap : 4000000000ull;
   p.st = a.st;
-  const int ntiles = (a.N / BN) * (a.M / BM);
-  k_split_gemm<<<ntiles, NTHREADS, SMEM_BYTES, s>>>(mAhi, mAlo, mBhi, mBlo, p);
+  const int ntiles = (a.N / G::BN) * (a.M / BM);
+  k_split_gemm<G><<<ntiles, NTHREADS, G::SMEM, s>>>(mAhi, mAlo, mBhi, mBlo, p);
   return cudaGetLastError();
 }
+
+int split_gemm_tile_n() { return ScreenCfg::BN; }
+int split_gemm_tile_k() { return ScreenCfg::BK; }
 
 }  // namespace lc
 
@@ -454,7 +497,7 @@ extern "C" LC_API int lc_split_gemm_f32(const float* A, const float* B, int M, i
   if (!A || !B || !D || M < 1 || N < 1 || K < 1) return LC_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!tcgen05_available()) return LC_ERR_CUDA;
-  const int Mp = round_up(M, BM), Np = round_up(N, BN), Kp = round_up(K, BK);
+  const int Mp = round_up(M, BM), Np = round_up(N, ScreenCfg::BN), Kp = round_up(K, ScreenCfg::BK);
   const size_t nA = (size_t)Mp * Kp, nB = (size_t)Np * Kp, nD = (size_t)Mp * Np;
   char* ws = nullptr;
   const size_t bytes = 4 * ((nA + nB) * 2 + 256) + nD * 4 + sizeof(DevStatus) + 1024;
@@ -727,7 +770,8 @@ extern "C" LC_API int lc_split_gemm_f32_noalloc(const float* A, const float* B, 
   using namespace lc;
   if (!A || !B || !D || M < 1 || N < 1 || K < 1) return LC_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const size_t Mp = (size_t)round_up(M, BM), Np = (size_t)round_up(N, BN), Kp = (size_t)round_up(K, BK);
+  const size_t Mp = (size_t)round_up(M, BM), Np = (size_t)round_up(N, ScreenCfg::BN),
+               Kp = (size_t)round_up(K, ScreenCfg::BK);
   // layout inside the scratch array, every region 256-byte aligned
   size_t off = 0;
   auto place = [&](size_t bytes) { const size_t at = off; off = (off + bytes + 255) & ~size_t(255); return at; };
