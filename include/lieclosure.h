@@ -72,7 +72,11 @@ typedef struct {
   double tau_screen;          /* mixed mode: relative residual below which a
                                  screened candidate is rejected without the FP64
                                  recheck; 0 = default (1e-3) */
-  int block_k;                /* candidates per block; 0 = automatic */
+  int block_k;                /* candidates per block once the basis stops
+                                 growing; 0 = automatic (16384 mixed, 2048 FP64,
+                                 capped by an 8 GB buffer budget) */
+  int block_k_growth;         /* candidates per block while the basis grows;
+                                 0 = automatic (1024) */
   int saturation_exit;        /* nonzero: stop once |V| reaches the largest
                                  possible dimension (d^2 - 1, plus one if a
                                  generator has a trace); not in the paper,

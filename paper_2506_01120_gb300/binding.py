@@ -47,7 +47,7 @@ class LieClosureError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("eta_abs", ctypes.c_double), ("tau_screen", ctypes.c_double),
-                ("block_k", ctypes.c_int), ("saturation_exit", ctypes.c_int), ("spin_cap", ctypes.c_longlong),
+                ("block_k", ctypes.c_int), ("block_k_growth", ctypes.c_int), ("saturation_exit", ctypes.c_int), ("spin_cap", ctypes.c_longlong),
                 ("max_candidates", ctypes.c_longlong), ("verbose", ctypes.c_int), ("profile", ctypes.c_int),
                 ("fault_inject", ctypes.c_int)]
 

@@ -122,7 +122,7 @@ class Closure {
     K = std::max(K, k_);         // the generator pass is one block
     K_ = std::max(1, K);
     Kpad_ = round_up(K_, 128);
-    Kgrow_ = std::min(K_, 1024);
+    Kgrow_ = std::min(K_, o.block_k_growth > 0 ? o.block_k_growth : 1024);
     tau_ = o.tau_screen > 0 ? o.tau_screen : 1e-3;
     eta_ = o.eta_abs > 0 ? o.eta_abs : 1e-12;
     eta_screen_ = std::max(eta_, 1e-5);
@@ -586,7 +586,8 @@ class Closure {
 int check_args(const void* g, int k, int d, double tol, long long max_dim, const lc_options& o) {
   if (!g || k < 1 || d < 2 || !(tol > 0.0) || max_dim < 1) return LC_ERR_ARG;
   if (o.precision != LC_PREC_FP64 && o.precision != LC_PREC_MIXED_BF16X3) return LC_ERR_ARG;
-  if (o.block_k < 0 || o.tau_screen < 0 || o.eta_abs < 0 || o.max_candidates < 0) return LC_ERR_ARG;
+  if (o.block_k < 0 || o.block_k_growth < 0 || o.tau_screen < 0 || o.eta_abs < 0 || o.max_candidates < 0)
+    return LC_ERR_ARG;
   if ((long long)d * d > (1ll << 31) / 2) return LC_ERR_ARG;
   return LC_OK;
 }

@@ -50,9 +50,34 @@ def test_host_only_calls(built_lib):
     assert "sm_103a" in binding.version()
 
 
+def test_struct_layouts_match_compiled_header(tmp_path):
+    """Every field offset of the ctypes mirrors equals offsetof() in C."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lieclosure.h"', 'int main(void) {']
+    for cname, py in (("lc_options", binding.Options), ("lc_report", binding.Report)):
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in (("lc_options", binding.Options), ("lc_report", binding.Report)):
+        assert got[(cname, "size")] == ctypes.sizeof(py)
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
 def test_struct_layouts_match_header():
     """ctypes mirrors of lc_options / lc_report have the C sizes."""
-    assert ctypes.sizeof(binding.Options) == 4 + 4 + 8 + 8 + 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4
+    assert ctypes.sizeof(binding.Options) == 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4
     assert ctypes.sizeof(binding.Report) == 8 * 8 + 8 * 5 + 8 + 8 + 8 + 8 + 8 * 6 + 4 * 2
 
 
