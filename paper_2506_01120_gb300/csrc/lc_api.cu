@@ -101,6 +101,7 @@ struct HostMirror {
   DevStatus st;
   double maxdev, maxabs;
   int nonfinite;
+  int nnz;
 };
 
 class Closure {
@@ -199,7 +200,7 @@ class Closure {
   double t_last_accept_ = 0.0;
   // device buffers
   double *G64_ = nullptr, *V64_ = nullptr, *H64_ = nullptr, *S64_ = nullptr, *R64_ = nullptr, *beta64_ = nullptr;
-  double *hn2_ = nullptr, *rn2_ = nullptr, *hnf_ = nullptr, *rnf_ = nullptr, *chk_ = nullptr;
+  double *hn2_ = nullptr, *rn2_ = nullptr, *hnf_ = nullptr, *rnf_ = nullptr, *chk_ = nullptr, *hn2c64_ = nullptr;
   int *idx_ = nullptr, *nonfinite_ = nullptr, *need_ = nullptr;
   unsigned int* bar_ = nullptr;
   double* ws64_ = nullptr;
@@ -233,6 +234,9 @@ class Closure {
       S64_ = ar_.take<double>((size_t)K_ * ldp_);
       hn2_ = ar_.take<double>(K_);
       rn2_ = ar_.take<double>(K_);
+      hn2c64_ = ar_.take<double>(K_);
+      nz_idx_ = ar_.take<int>(K_);
+      nnz_ = ar_.take<int>(1);
     } else {
       Vhi_ = ar_.take<__nv_bfloat16>((size_t)ncap_pad_ * ldp_);
       Vlo_ = ar_.take<__nv_bfloat16>((size_t)ncap_pad_ * ldp_);
@@ -463,23 +467,35 @@ class Closure {
     ph_begin();
     LC_TRY(bracket_fp64(V64_, d_, ldp_, t0, nullptr, kb, H64_, ldp_, s_));
     ph_end(PH_BRACKET);
+    // zero brackets (commuting pairs) are rejected without a projection; the
+    // rest are packed into consecutive rows of S64
     ph_begin();
     LC_TRY(rownorm2_f64(kb, P_, H64_, ldp_, hn2_, s_));
-    LC_TRY(gemm_nt_f64(kb, (int)N_, P_, H64_, ldp_, V64_, ldp_, beta64_, (int)ncap_, s_, ws64_, kWs64));
+    LC_TRY(compact_nonzero_f64(hn2_, kb, eta_ * eta_, nz_idx_, nnz_, hn2c64_, s_));
+    LC_TRY(cudaMemcpyAsync(&host_->nnz, nnz_, sizeof(int), cudaMemcpyDeviceToHost, s_));
+    LC_TRY(cudaStreamSynchronize(s_));
+    const int nnz = host_->nnz;
+    if (nnz > 0) LC_TRY(gather_rows_f64(H64_, ldp_, nz_idx_, nnz, P_, S64_, ldp_, s_));
+    ph_end(PH_SCREEN);
+    launches_ += 4;
+    if (nnz == 0) {
+      nonzero_ += 0;
+      return LC_OK;
+    }
+    ph_begin();
+    LC_TRY(gemm_nt_f64(nnz, (int)N_, P_, S64_, ldp_, V64_, ldp_, beta64_, (int)ncap_, s_, ws64_, kWs64));
     ph_end(PH_GEMM1);
     ph_begin();
-    LC_TRY(cudaMemcpy2DAsync(S64_, sizeof(double) * ldp_, H64_, sizeof(double) * ldp_, sizeof(double) * P_, kb,
-                             cudaMemcpyDeviceToDevice, s_));
-    LC_TRY(gemm_nn_sub_f64(kb, P_, (int)N_, beta64_, (int)ncap_, V64_, ldp_, S64_, ldp_, s_, ws64_, kWs64));
-    LC_TRY(rownorm2_f64(kb, P_, S64_, ldp_, rn2_, s_));
+    LC_TRY(gemm_nn_sub_f64(nnz, P_, (int)N_, beta64_, (int)ncap_, V64_, ldp_, S64_, ldp_, s_, ws64_, kWs64));
+    LC_TRY(rownorm2_f64(nnz, P_, S64_, ldp_, rn2_, s_));
     ph_end(PH_GEMM2);
     // one FP64 projection pass: ||r1|| <= tol/2 ||h|| implies the two-pass
     // residual is below tol ||h|| as well, so such candidates are dependent
     const double tau = 0.5 * tol_;
     ph_begin();
-    LC_TRY(screen_compact_f64(hn2_, rn2_, kb, eta_ * eta_, tau * tau, idx_, stats_, s_));
+    LC_TRY(screen_compact_f64(hn2c64_, rn2_, nnz, eta_ * eta_, tau * tau, idx_, stats_, s_, nullptr, nz_idx_));
     ph_end(PH_SCREEN);
-    launches_ += 6;
+    launches_ += 4;
     return after_screen(t0);
   }
 

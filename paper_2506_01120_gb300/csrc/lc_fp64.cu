@@ -520,6 +520,44 @@ __global__ void k_need_pass2(int f, const double* __restrict__ hn2, const double
   if (threadIdx.x == 0) *need = any;
 }
 
+// ordered list of candidates with hn2 > eta2 (one CTA of 1024 threads); the
+// FP64 screen uses it to skip zero brackets, as the mixed screen does
+__global__ void __launch_bounds__(1024) k_compact_nonzero_f64(const double* __restrict__ hn2, int count, double eta2,
+                                                              int* __restrict__ nz_idx, int* __restrict__ nnz,
+                                                              double* __restrict__ hn2c) {
+  __shared__ int wsum[32];
+  __shared__ int base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c0 = 0; c0 < count; c0 += 1024) {
+    const int c = c0 + threadIdx.x;
+    const int f = (c < count && hn2[c] > eta2) ? 1 : 0;
+    const unsigned mask = __ballot_sync(0xffffffffu, f);
+    const int pre = __popc(mask & ((1u << lane) - 1u));
+    if (lane == 0) wsum[w] = __popc(mask);
+    __syncthreads();
+    if (w == 0) {
+      int v = wsum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
+      }
+      wsum[lane] = v;
+    }
+    __syncthreads();
+    if (f) {
+      const int at = base + (w ? wsum[w - 1] : 0) + pre;
+      nz_idx[at] = c;
+      hn2c[at] = hn2[c];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) base += wsum[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *nnz = base;
+}
+
 __global__ void k_zero_stats(DevStats* stats, int ncur) {
   stats->ncur = ncur;
   stats->naccepted = 0;
@@ -632,8 +670,8 @@ cudaError_t gather_rows_f64(const double* src, int lds, const int* idx, int coun
 }
 
 cudaError_t screen_compact_f64(const double* hn2, const double* rn2, int count, double eta2, double tau2, int* idx,
-                               DevStats* stats, cudaStream_t s) {
-  k_screen_compact<double><<<1, 1024, 0, s>>>(hn2, rn2, count, eta2, tau2, idx, stats, nullptr, nullptr);
+                               DevStats* stats, cudaStream_t s, const int* count_dev, const int* map) {
+  k_screen_compact<double><<<1, 1024, 0, s>>>(hn2, rn2, count, eta2, tau2, idx, stats, count_dev, map);
   return cudaGetLastError();
 }
 
@@ -672,6 +710,12 @@ cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2
 cudaError_t need_pass2(int f, const double* hn2, const double* rn2, double eta2, double tol, int* need,
                        cudaStream_t s) {
   k_need_pass2<<<1, 256, 0, s>>>(f, hn2, rn2, eta2, tol, need);
+  return cudaGetLastError();
+}
+
+cudaError_t compact_nonzero_f64(const double* hn2, int count, double eta2, int* nz_idx, int* nnz, double* hn2c,
+                                cudaStream_t s) {
+  k_compact_nonzero_f64<<<1, 1024, 0, s>>>(hn2, count, eta2, nz_idx, nnz, hn2c);
   return cudaGetLastError();
 }
 

@@ -98,7 +98,11 @@ cudaError_t gather_rows_f64(const double* src, int lds, const int* idx, int coun
 // flags candidates with hn2 > eta^2 and rn2 > tau^2 hn2; writes the flagged
 // candidate positions in order to idx and their count to stats->nflag
 cudaError_t screen_compact_f64(const double* hn2, const double* rn2, int count, double eta2,
-                               double tau2, int* idx, DevStats* stats, cudaStream_t s);
+                               double tau2, int* idx, DevStats* stats, cudaStream_t s,
+                               const int* count_dev = nullptr, const int* map = nullptr);
+// ordered indices of the candidates with hn2 > eta2, their count (*nnz) and norms
+cudaError_t compact_nonzero_f64(const double* hn2, int count, double eta2, int* nz_idx, int* nnz,
+                                double* hn2c, cudaStream_t s);
 // count_dev (optional): live count on the device; map (optional): idx[i] = map[position]
 cudaError_t screen_compact_f32(const float* hn2, const float* rn2, int count, float eta2,
                                float tau2, int* idx, DevStats* stats, cudaStream_t s,
