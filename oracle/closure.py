@@ -16,6 +16,8 @@ Functions and the passage each follows
                       the Corollary and the equation after it).
 * ``alg4_orthonormalization`` -- Algorithm 4 (dimension-only orthonormalisation
                       method), O1.
+* ``alg3_orthonormalization`` -- Algorithm 3 (orthonormalisation keeping the
+                      generators and nested brackets B beside V).
 * ``alg1_rank``    -- Algorithm 1 with the independence test done by matrix rank
                       via SVD (Section 3, the rank method), O2.
 * ``pauli_closure`` -- exact closure of a set of Pauli strings by set
@@ -199,6 +201,82 @@ def alg4_orthonormalization(generators: np.ndarray, tol: float, eta_abs: float =
     res.l, res.m = l, m
     res.t_total += time.perf_counter() - t0
     return res
+
+
+# ------------------------------------------------------------- Algorithm 3
+@dataclass
+class Alg3Result:
+    B: np.ndarray          # (dim, d, d): the generators and nested brackets kept
+    V: np.ndarray          # (dim, d, d): orthonormal basis of the same span
+    dim: int
+    parents: list          # per element of B: None (a generator) or (l, m)
+    candidates: int = 0
+
+
+def alg3_orthonormalization(generators: np.ndarray, tol: float, eta_abs: float = 1e-12,
+                            saturation_exit: bool = False) -> Alg3Result:
+    """Algorithm 3: the orthonormalisation method keeping the original basis.
+
+    Two tuples grow together: B holds the accepted generators and nested
+    brackets themselves, V their orthonormalised versions.  Brackets are formed
+    from B; each is tested against V with the same rule as Algorithm 4
+    (two classical Gram-Schmidt passes, relative tolerance, absolute floor).
+    """
+    k, d, _ = generators.shape
+    cap = 2 * d * d
+    B = np.zeros((min(cap, 64), d, d), dtype=np.complex128)
+    V = np.zeros_like(B)
+    parents: list = []
+    n = 0
+    count = 0
+
+    def grow(arr, n):
+        out = np.zeros((max(4, 2 * n),) + arr.shape[1:], dtype=np.complex128)
+        out[:n] = arr[:n]
+        return out
+
+    def test(h):
+        hn = norm(h)
+        if hn <= eta_abs:
+            return None
+        r = project_out(V[:n], h)
+        r = project_out(V[:n], r)
+        rn = norm(r)
+        return r / rn if rn > tol * hn else None
+
+    for g in generators:
+        g = np.asarray(g, dtype=np.complex128)
+        count += 1
+        v = test(g)
+        if v is not None:
+            if n >= cap:
+                raise CapacityError("closure dimension would exceed 2 d^2")
+            if n == B.shape[0]:
+                B, V = grow(B, n), grow(V, n)
+            B[n], V[n] = g, v
+            parents.append(None)
+            n += 1
+    bound = max_dim_bound(generators) if saturation_exit else None
+    l, m = 1, 0
+    while l < n:
+        if bound is not None and n >= bound:
+            break
+        h = bracket(B[l], B[m])
+        count += 1
+        v = test(h)
+        if v is not None:
+            if n >= cap:
+                raise CapacityError("closure dimension would exceed 2 d^2")
+            if n == B.shape[0]:
+                B, V = grow(B, n), grow(V, n)
+            B[n], V[n] = h, v
+            parents.append((l, m))
+            n += 1
+        m += 1
+        if m == l:
+            l += 1
+            m = 0
+    return Alg3Result(B=B[:n], V=V[:n], dim=n, parents=parents, candidates=count)
 
 
 # ------------------------------------------------------------- Algorithm 1

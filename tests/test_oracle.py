@@ -258,3 +258,34 @@ def test_planted_mistake_is_caught(monkeypatch, mistake):
         monkeypatch.setattr(oc, "coefficients",
                             lambda V, h: np.einsum("ljk,jk->l", V.conj(), h))
     assert not _pins_pass()
+
+
+# ------------------------------------------------------------- Algorithm 3
+@pytest.mark.parametrize("case", ["so6", "su8", "rand_d4", "pauli"])
+def test_alg3_same_algebra_as_alg4(case):
+    """Algorithm 3 keeps the generators and nested brackets B; the paper notes
+    that it yields the same algebra as Algorithm 4 (Section 3.2).  Pins: equal
+    dimension, span(B) = span(V) = the Algorithm 4 span, V orthonormal, and every
+    kept element after the generators is literally the bracket of its parents."""
+    if case == "so6":
+        g = inputs.generators_from_labels(inputs.so2n_chain_labels(3)); expect = 15
+    elif case == "su8":
+        g = inputs.generators_from_labels(inputs.su2n_chain_labels(3)); expect = 63
+    elif case == "rand_d4":
+        g = inputs.random_set(4, 2, seed=3); expect = 15
+    else:
+        rng = np.random.default_rng(9)
+        labels = inputs.random_pauli_labels(3, 4, rng)
+        g = inputs.generators_from_labels(labels); expect = len(oc.pauli_closure(labels))
+    r3 = oc.alg3_orthonormalization(g, 1e-10)
+    r4 = oc.alg4_orthonormalization(g, 1e-10)
+    assert r3.dim == r4.dim == expect
+    assert oc.ortho_defect(r3.V) < 1e-12
+    assert oc.span_distance(r3.V, r4.basis) < 1e-9
+    assert oc.span_distance(r3.B, r3.V) < 1e-9
+    for i, par in enumerate(r3.parents):
+        if par is None:
+            assert any(np.array_equal(r3.B[i], x) for x in g)
+        else:
+            l, m = par
+            np.testing.assert_array_equal(r3.B[i], oc.bracket(r3.B[l], r3.B[m]))
