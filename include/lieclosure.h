@@ -169,6 +169,32 @@ LC_API int lie_closure_dev(const lc_c128* generators, int k, int d, double tol,
                     const lc_options* opt, lc_report* rep, void* stream);
 
 /*
+ * lie_closure_alg3 -- Algorithm 3 of the paper (Section 3.2): the
+ * orthonormalisation method that keeps, beside the orthonormal basis V, the
+ * basis B made of the accepted generators and nested brackets themselves.
+ * Brackets are formed from elements of B ([B[l], B[m]], same pair order as
+ * lie_closure) and tested against V with the same rule; an accepted bracket h
+ * is appended to B as it is and to V as h_perp / ||h_perp||.  span(B) = span(V)
+ * is the same algebra lie_closure returns.
+ *
+ * nested_out : host buffer for max_dim x d x d complex128 receiving B (or NULL).
+ * basis_out  : host buffer receiving V (or NULL).
+ * Other arguments, statuses and the report are those of lie_closure.  B is
+ * not normalised: its elements are the brackets as formed, so their norms can
+ * grow with nesting depth.
+ */
+LC_API int lie_closure_alg3(const lc_c128* generators, int k, int d, double tol,
+                     lc_c128* nested_out, lc_c128* basis_out, long long* dim_out,
+                     long long max_dim, const lc_options* opt, lc_report* rep);
+
+/* lie_closure_alg3_dev -- as lie_closure_alg3 with device buffers and a stream
+ * (conventions of lie_closure_dev). */
+LC_API int lie_closure_alg3_dev(const lc_c128* generators, int k, int d, double tol,
+                         lc_c128* nested_out, lc_c128* basis_out, long long* dim_out,
+                         long long max_dim, const lc_options* opt, lc_report* rep,
+                         void* stream);
+
+/*
  * lie_closure_batched -- Algorithm 4 on nsets independent generator sets
  * (Section 3.2 applied per set), host buffers.
  *

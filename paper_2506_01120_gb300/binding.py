@@ -32,7 +32,8 @@ PRECISIONS = {"fp64": LC_PREC_FP64, "mixed": LC_PREC_MIXED_BF16X3}
 
 # every symbol the public headers declare
 EXPORTED = ["lc_default_options", "lc_status_string", "lc_version", "lie_closure", "lie_closure_dev",
-            "lie_closure_batched", "lc_split_gemm_f32", "lc_split_gemm_f32_noalloc"]
+            "lie_closure_batched", "lie_closure_alg3", "lie_closure_alg3_dev", "lc_split_gemm_f32",
+            "lc_split_gemm_f32_noalloc"]
 
 
 class LibraryNotBuilt(RuntimeError):
@@ -101,6 +102,12 @@ def lib():
                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Options),
                                           ctypes.POINTER(Report)]
         L.lie_closure_batched.restype = ctypes.c_int
+        L.lie_closure_alg3.argtypes = [c_p, ctypes.c_int, ctypes.c_int, ctypes.c_double, c_p, c_p,
+                                       ctypes.POINTER(ctypes.c_longlong), ctypes.c_longlong,
+                                       ctypes.POINTER(Options), ctypes.POINTER(Report)]
+        L.lie_closure_alg3.restype = ctypes.c_int
+        L.lie_closure_alg3_dev.argtypes = L.lie_closure_alg3.argtypes + [c_p]
+        L.lie_closure_alg3_dev.restype = ctypes.c_int
         L.lc_split_gemm_f32.argtypes = [c_p, c_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_p, c_p]
         L.lc_split_gemm_f32.restype = ctypes.c_int
         L.lc_split_gemm_f32_noalloc.argtypes = L.lc_split_gemm_f32.argtypes
@@ -158,6 +165,27 @@ def lie_closure(generators, tol: float, max_dim: int | None = None, return_basis
     _check(st, check)
     n = int(dim.value)
     return ClosureResult(n, basis[:n] if basis is not None else None, st, rep.as_dict())
+
+
+def lie_closure_alg3(generators, tol: float, max_dim: int | None = None, check: bool = True,
+                     precision="mixed", **opts):
+    """Algorithm 3 on host arrays: returns (B, V, status, report) with B the kept
+    generators and nested brackets and V the orthonormal basis."""
+    g = np.ascontiguousarray(generators, dtype=np.complex128)
+    if g.ndim != 3 or g.shape[1] != g.shape[2]:
+        raise ValueError("generators must have shape (k, d, d)")
+    k, d, _ = g.shape
+    cap = int(max_dim) if max_dim is not None else d * d
+    B = np.zeros((cap, d, d), dtype=np.complex128)
+    V = np.zeros((cap, d, d), dtype=np.complex128)
+    dim = ctypes.c_longlong(0)
+    rep = Report()
+    o = make_options(precision, **opts)
+    st = lib().lie_closure_alg3(g.ctypes.data, k, d, float(tol), B.ctypes.data, V.ctypes.data, ctypes.byref(dim),
+                                cap, ctypes.byref(o), ctypes.byref(rep))
+    _check(st, check)
+    n = int(dim.value)
+    return B[:n], V[:n], st, rep.as_dict()
 
 
 def lie_closure_dev(generators, tol: float, max_dim: int | None = None, basis_out=None, stream=None,

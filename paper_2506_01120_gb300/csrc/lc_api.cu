@@ -106,8 +106,8 @@ struct HostMirror {
 
 class Closure {
  public:
-  Closure(int k, int d, double tol, long long ncap, const lc_options& o, cudaStream_t s)
-      : k_(k), d_(d), tol_(tol), ncap_(ncap), opt(o), s_(s) {
+  Closure(int k, int d, double tol, long long ncap, const lc_options& o, cudaStream_t s, bool alg3 = false)
+      : k_(k), d_(d), tol_(tol), ncap_(ncap), opt(o), s_(s), alg3_(alg3) {
     P_ = d * d;
     mixed_ = (o.precision == LC_PREC_MIXED_BF16X3);
     // pad to the screening GEMM's N tile (it runs over both the basis and the
@@ -131,7 +131,8 @@ class Closure {
     tc_bracket_ = mixed_ && (bracket_tc_supported(d) || big_bracket_);
   }
 
-  int run(const double2* d_gens, double2* d_basis_out, long long* dim_out, lc_report* rep) {
+  int run(const double2* d_gens, double2* d_basis_out, long long* dim_out, lc_report* rep,
+          double2* d_nested_out = nullptr) {
     const double t_start = now_s();
     t_last_accept_ = 0.0;
     int rc = setup(d_gens);
@@ -140,6 +141,10 @@ class Closure {
     if (rc == LC_OK || rc == LC_ERR_CAPACITY) {
       if (d_basis_out && N_ > 0) {
         cudaError_t e = unpack_basis(V64_, (int)N_, d_, ldp_, d_basis_out, s_);
+        if (e != cudaSuccess) rc = LC_ERR_CUDA;
+      }
+      if (alg3_ && d_nested_out && N_ > 0) {
+        cudaError_t e = unpack_basis(B64_, (int)N_, d_, ldp_, d_nested_out, s_);
         if (e != cudaSuccess) rc = LC_ERR_CUDA;
       }
     }
@@ -194,7 +199,11 @@ class Closure {
   lc_options opt;
   cudaStream_t s_;
   bool mixed_;
+  bool alg3_;            // Algorithm 3: brackets of B, B kept beside V
+  double *B64_ = nullptr, *Hraw_ = nullptr, *bn2_ = nullptr;
   Arena ar_;
+  // rows the brackets are formed from: V (Algorithm 4) or B (Algorithm 3)
+  const double* src() const { return alg3_ ? B64_ : V64_; }
   HostMirror* host_ = nullptr;
   long long N_ = 0, t_ = 0, checked_ = 0, nonzero_ = 0, flagged_ = 0, blocks_ = 0;
   double t_last_accept_ = 0.0;
@@ -229,6 +238,11 @@ class Closure {
     need_ = ar_.take<int>(1);
     bar_ = ar_.take<unsigned int>(2);
     ws64_ = ar_.take<double>(kWs64);
+    if (alg3_) {
+      B64_ = ar_.take<double>((size_t)ncap_ * ldp_);
+      Hraw_ = ar_.take<double>((size_t)K_ * ldp_);
+      bn2_ = ar_.take<double>(ncap_);
+    }
     if (!mixed_) {
       H64_ = ar_.take<double>((size_t)K_ * ldp_);
       S64_ = ar_.take<double>((size_t)K_ * ldp_);
@@ -298,6 +312,8 @@ class Closure {
     if (ldp_ > P_) {
       // padding columns of the FP64 rows stay zero
       LC_TRY(cudaMemset2DAsync(V64_ + P_, sizeof(double) * ldp_, 0, sizeof(double) * (ldp_ - P_), ncap_, s_));
+      if (alg3_)
+        LC_TRY(cudaMemset2DAsync(B64_ + P_, sizeof(double) * ldp_, 0, sizeof(double) * (ldp_ - P_), ncap_, s_));
     }
     LC_TRY(cudaMemsetAsync(st_, 0, sizeof(DevStatus), s_));
     LC_TRY(cudaMemsetAsync(bar_, 0, 2 * sizeof(unsigned int), s_));
@@ -401,6 +417,9 @@ class Closure {
   int accept_rows(int f) {
     flagged_ += f;
     ph_begin();
+    if (alg3_)   // the raw bracket (or generator) is what Algorithm 3 appends to B
+      LC_TRY(cudaMemcpy2DAsync(Hraw_, sizeof(double) * ldp_, R64_, sizeof(double) * ldp_, sizeof(double) * P_, f,
+                               cudaMemcpyDeviceToDevice, s_));
     LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, hnf_, s_));
     const int n0 = (int)N_;
     if (n0 > 0) {
@@ -417,7 +436,8 @@ class Closure {
     }
     LC_TRY(zero_stats(stats_, n0, s_));
     LC_TRY(accept_seq(f, R64_, ldp_, rnf_, hnf_, tol_, eta_ * eta_, V64_, ldp_, (int)ncap_, P_, stats_, st_, bar_,
-                      opt.spin_cap, s_, opt.fault_inject ? 1 : 0));
+                      opt.spin_cap, s_, opt.fault_inject ? 1 : 0, alg3_ ? Hraw_ : nullptr, alg3_ ? B64_ : nullptr,
+                      alg3_ ? bn2_ : nullptr));
     launches_ += 4;
     ph_end(PH_ACCEPT);
     int rc = sync_read();
@@ -428,7 +448,7 @@ class Closure {
       LC_TRY(split_rows(V64_, ldp_, n0, (int)n1, P_, Vhi_, Vlo_, ldp_, VThi_, VTlo_, ncap_pad_, s_));
       launches_ += 1;
       if (tc_bracket_) {
-        LC_TRY(build_embedding(V64_, ldp_, n0, (int)n1, d_, Ehi_, Elo_, s_, big_bracket_ ? 1 : 0));
+        LC_TRY(build_embedding(src(), ldp_, n0, (int)n1, d_, Ehi_, Elo_, s_, big_bracket_ ? 1 : 0));
         launches_ += 1;
       }
       ph_end(PH_OTHER);
@@ -452,7 +472,7 @@ class Closure {
     if (f > 0) {
       if (mixed_) {
         ph_begin();
-        LC_TRY(bracket_fp64(V64_, d_, ldp_, t0, idx_, f, R64_, ldp_, s_));
+        LC_TRY(bracket_fp64(src(), d_, ldp_, t0, idx_, f, R64_, ldp_, s_));
         ph_end(PH_ACCEPT);
       } else {
         LC_TRY(gather_rows_f64(H64_, ldp_, idx_, f, P_, R64_, ldp_, s_));
@@ -465,7 +485,7 @@ class Closure {
 
   int block_fp64(long long t0, int kb) {
     ph_begin();
-    LC_TRY(bracket_fp64(V64_, d_, ldp_, t0, nullptr, kb, H64_, ldp_, s_));
+    LC_TRY(bracket_fp64(src(), d_, ldp_, t0, nullptr, kb, H64_, ldp_, s_));
     ph_end(PH_BRACKET);
     // zero brackets (commuting pairs) are rejected without a projection; the
     // rest are packed into consecutive rows of S64
@@ -506,14 +526,15 @@ class Closure {
     } else if (tc_bracket_) {
       LC_TRY(bracket_tc(Ehi_, Elo_, ncap_, d_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, opt.spin_cap, st_, s_));
     } else {
-      LC_TRY(bracket_mixed(V64_, d_, ldp_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, s_));
+      LC_TRY(bracket_mixed(src(), d_, ldp_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, s_));
     }
     ph_end(PH_BRACKET);
     // candidates with a (numerically) zero bracket are rejected outright; the
     // rest are packed into consecutive rows so the GEMMs skip the zeros
     const float es = (float)eta_screen_, ts = (float)tau_;
     ph_begin();
-    LC_TRY(compact_nonzero(hn2f_, kb, es * es, nz_idx_, nnz_, s_));
+    // (B is not normalised: for Algorithm 3 the floor scales with ||B_l|| ||B_m||)
+    LC_TRY(compact_nonzero(hn2f_, kb, es * es, nz_idx_, nnz_, s_, alg3_ ? bn2_ : nullptr, t0));
     LC_TRY(gather_candidates(Hhi_, Hlo_, ldp_, hn2f_, nz_idx_, nnz_, kb, ldp_, Chi_, Clo_, hn2c_, s_));
     ph_end(PH_SCREEN);
     const int M = round_up(kb, 128);
@@ -609,10 +630,11 @@ int check_args(const void* g, int k, int d, double tol, long long max_dim, const
 }
 
 int closure_device(const double2* d_gens, int k, int d, double tol, double2* d_basis, long long* dim_out,
-                   long long max_dim, const lc_options& o, lc_report* rep, cudaStream_t s) {
+                   long long max_dim, const lc_options& o, lc_report* rep, cudaStream_t s, bool alg3 = false,
+                   double2* d_nested = nullptr) {
   const long long ncap = std::min<long long>(max_dim, (long long)d * d);
-  Closure c(k, d, tol, ncap, o, s);
-  int rc = c.run(d_gens, d_basis, dim_out, rep);
+  Closure c(k, d, tol, ncap, o, s, alg3);
+  int rc = c.run(d_gens, d_basis, dim_out, rep, d_nested);
   if (rc == LC_OK && max_dim < (long long)d * d && dim_out && *dim_out > max_dim) rc = LC_ERR_CAPACITY;
   return rc;
 }
@@ -620,14 +642,16 @@ int closure_device(const double2* d_gens, int k, int d, double tol, double2* d_b
 // One closure from host buffers on stream s (generators copied in, basis
 // copied out), used by lie_closure and by each batched worker.
 int closure_host(const lc_c128* generators, int k, int d, double tol, lc_c128* basis_out, long long* dim_out,
-                 long long max_dim, const lc_options& o, lc_report* rep, cudaStream_t s) {
+                 long long max_dim, const lc_options& o, lc_report* rep, cudaStream_t s, bool alg3 = false,
+                 lc_c128* nested_out = nullptr) {
   if (dim_out) *dim_out = 0;
   int rc = check_args(generators, k, d, tol, max_dim, o);
   if (rc != LC_OK) return rc;
   const size_t gbytes = sizeof(double2) * (size_t)k * d * d;
   const long long ncap = std::min<long long>(max_dim, (long long)d * d);
   const size_t bbytes = basis_out ? sizeof(double2) * (size_t)ncap * d * d : 0;
-  double2 *dg = nullptr, *db = nullptr;
+  const size_t nbytes = (alg3 && nested_out) ? sizeof(double2) * (size_t)ncap * d * d : 0;
+  double2 *dg = nullptr, *db = nullptr, *dn = nullptr;
   cudaMemPool_t pool;
   if (get_pool(&pool) != cudaSuccess) rc = LC_ERR_CUDA;
   if (rc == LC_OK && cudaMallocFromPoolAsync(reinterpret_cast<void**>(&dg), gbytes, pool, s) != cudaSuccess)
@@ -635,17 +659,21 @@ int closure_host(const lc_c128* generators, int k, int d, double tol, lc_c128* b
   if (rc == LC_OK && bbytes &&
       cudaMallocFromPoolAsync(reinterpret_cast<void**>(&db), bbytes, pool, s) != cudaSuccess)
     rc = LC_ERR_OOM;
+  if (rc == LC_OK && nbytes &&
+      cudaMallocFromPoolAsync(reinterpret_cast<void**>(&dn), nbytes, pool, s) != cudaSuccess)
+    rc = LC_ERR_OOM;
   if (rc == LC_OK && cudaMemcpyAsync(dg, generators, gbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
     rc = LC_ERR_CUDA;
   long long dim = 0;
-  if (rc == LC_OK) rc = closure_device(dg, k, d, tol, db, &dim, max_dim, o, rep, s);
-  if ((rc == LC_OK || rc == LC_ERR_CAPACITY) && db && dim > 0) {
-    if (cudaMemcpyAsync(basis_out, db, sizeof(double2) * (size_t)std::min(dim, ncap) * d * d,
-                        cudaMemcpyDeviceToHost, s) != cudaSuccess)
-      rc = LC_ERR_CUDA;
+  if (rc == LC_OK) rc = closure_device(dg, k, d, tol, db, &dim, max_dim, o, rep, s, alg3, dn);
+  if ((rc == LC_OK || rc == LC_ERR_CAPACITY) && dim > 0) {
+    const size_t out = sizeof(double2) * (size_t)std::min(dim, ncap) * d * d;
+    if (db && cudaMemcpyAsync(basis_out, db, out, cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = LC_ERR_CUDA;
+    if (dn && cudaMemcpyAsync(nested_out, dn, out, cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = LC_ERR_CUDA;
   }
   if (dg) cudaFreeAsync(dg, s);
   if (db) cudaFreeAsync(db, s);
+  if (dn) cudaFreeAsync(dn, s);
   if (cudaStreamSynchronize(s) != cudaSuccess && rc == LC_OK) rc = LC_ERR_CUDA;
   if (dim_out) *dim_out = dim;
   return rc;
@@ -755,6 +783,33 @@ int lie_closure(const lc_c128* generators, int k, int d, double tol, lc_c128* ba
   rc = closure_host(generators, k, d, tol, basis_out, dim_out, max_dim, o, rep, s);
   cudaStreamDestroy(s);
   return rc;
+}
+
+int lie_closure_alg3(const lc_c128* generators, int k, int d, double tol, lc_c128* nested_out, lc_c128* basis_out,
+                     long long* dim_out, long long max_dim, const lc_options* opt, lc_report* rep) {
+  lc_options o;
+  if (opt) o = *opt; else lc_default_options(&o);
+  if (dim_out) *dim_out = 0;
+  int rc = check_args(generators, k, d, tol, max_dim, o);
+  if (rc != LC_OK) return rc;
+  cudaStream_t s;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return LC_ERR_CUDA;
+  rc = closure_host(generators, k, d, tol, basis_out, dim_out, max_dim, o, rep, s, true, nested_out);
+  cudaStreamDestroy(s);
+  return rc;
+}
+
+int lie_closure_alg3_dev(const lc_c128* generators, int k, int d, double tol, lc_c128* nested_out,
+                         lc_c128* basis_out, long long* dim_out, long long max_dim, const lc_options* opt,
+                         lc_report* rep, void* stream) {
+  lc_options o;
+  if (opt) o = *opt; else lc_default_options(&o);
+  if (dim_out) *dim_out = 0;
+  int rc = check_args(generators, k, d, tol, max_dim, o);
+  if (rc != LC_OK) return rc;
+  return closure_device(reinterpret_cast<const double2*>(generators), k, d, tol,
+                        reinterpret_cast<double2*>(basis_out), dim_out, max_dim, o, rep,
+                        static_cast<cudaStream_t>(stream), true, reinterpret_cast<double2*>(nested_out));
 }
 
 int lie_closure_batched(int nsets, const lc_c128* const* generators, const int* k, const int* d, double tol,

@@ -453,7 +453,9 @@ __global__ void __launch_bounds__(256) k_accept_seq(int f, double* __restrict__ 
                                                     double* __restrict__ rn2, const double* __restrict__ hn2,
                                                     double tol, double eta2, double* __restrict__ V, int ldv,
                                                     int ncap, int P, DevStats* stats, DevStatus* st,
-                                                    unsigned int* bar, uint64_t limit_ns, int phantom) {
+                                                    unsigned int* bar, uint64_t limit_ns, int phantom,
+                                                    const double* __restrict__ Hraw, double* __restrict__ Bk,
+                                                    double* __restrict__ bn2) {
   __shared__ double red[33];
   __shared__ int slot, ok_smem;
   const unsigned int G = gridDim.x;
@@ -484,6 +486,12 @@ __global__ void __launch_bounds__(256) k_accept_seq(int f, double* __restrict__ 
       if (slot >= 0) {
         double* v = V + (long long)slot * ldv;
         for (int p = threadIdx.x; p < P; p += blockDim.x) v[p] = __ldcg(&ri[p]) * inv;
+        if (Bk) {   // Algorithm 3: the bracket itself joins B
+          const double* hr = Hraw + (long long)i * ldr;
+          double* b = Bk + (long long)slot * ldv;
+          for (int p = threadIdx.x; p < P; p += blockDim.x) b[p] = hr[p];
+          if (threadIdx.x == 0) bn2[slot] = h2;
+        }
       }
     }
     for (int j = i + 1 + (int)((blockIdx.x + G - (unsigned)((i + 1) % G)) % G); j < f; j += G) {
@@ -690,7 +698,7 @@ cudaError_t accept_step(int i, int f, double* R, int ldr, double* rn2, const dou
 
 cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2, double tol, double eta2, double* V,
                        int ldv, int ncap, int P, DevStats* stats, DevStatus* st, unsigned int* bar, long long spin_cap,
-                       cudaStream_t s, int phantom) {
+                       cudaStream_t s, int phantom, const double* Hraw, double* Bk, double* bn2) {
   if (f <= 0) return cudaSuccess;
   static std::once_flag once;
   static int nblocks = 1;
@@ -703,7 +711,8 @@ cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2
   });
   const int G = std::max(1, std::min(nblocks, f));
   uint64_t lim = spin_cap > 0 ? (uint64_t)spin_cap : 4000000000ull;
-  void* args[] = {&f, &R, &ldr, &rn2, (void*)&hn2, &tol, &eta2, &V, &ldv, &ncap, &P, &stats, &st, &bar, &lim, &phantom};
+  void* args[] = {&f,   &R,     &ldr,   &rn2, (void*)&hn2, &tol,    &eta2,          &V,  &ldv, &ncap, &P,
+                  &stats, &st, &bar, &lim, &phantom,    (void*)&Hraw, &Bk, &bn2};
   return cudaLaunchCooperativeKernel((const void*)k_accept_seq, dim3(G), dim3(256), args, 0, s);
 }
 

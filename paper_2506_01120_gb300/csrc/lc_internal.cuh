@@ -89,7 +89,8 @@ cudaError_t rownorm2_f64(int M, int N, const double* A, int lda, double* out, cu
 // launch (bar: two zeroed unsigned ints)
 cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2, double tol, double eta2,
                        double* V, int ldv, int ncap, int P, DevStats* stats, DevStatus* st,
-                       unsigned int* bar, long long spin_cap, cudaStream_t s, int phantom = 0);
+                       unsigned int* bar, long long spin_cap, cudaStream_t s, int phantom = 0,
+                       const double* Hraw = nullptr, double* Bk = nullptr, double* bn2 = nullptr);
 // *need = 1 iff some row needs a second Gram-Schmidt pass
 cudaError_t need_pass2(int f, const double* hn2, const double* rn2, double eta2, double tol, int* need,
                        cudaStream_t s);
@@ -130,7 +131,10 @@ cudaError_t bracket_mixed(const double* V, int d, int ldv, long long t0, int cou
 cudaError_t build_embedding(const double* V, int ldv, int r0, int r1, int d, __nv_bfloat16* Ehi,
                             __nv_bfloat16* Elo, cudaStream_t s, int perm = 0);
 // ordered indices of the candidates with hn2 > eta2; their count to *nnz (device)
-cudaError_t compact_nonzero(const float* hn2, int count, float eta2, int* nz_idx, int* nnz, cudaStream_t s);
+// (bn2, optional: squared norms of the bracket operands' rows; the floor is
+// then eta2 * bn2[l] * bn2[m] for the pair t0 + position)
+cudaError_t compact_nonzero(const float* hn2, int count, float eta2, int* nz_idx, int* nnz, cudaStream_t s,
+                            const double* bn2 = nullptr, long long t0 = 0);
 // rows nz_idx[0 .. *nnz) of H (and their norms) -> consecutive rows of C
 cudaError_t gather_candidates(const __nv_bfloat16* Hhi, const __nv_bfloat16* Hlo, int ldh, const float* hn2,
                               const int* nz_idx, const int* nnz, int count, int ncols, __nv_bfloat16* Chi,

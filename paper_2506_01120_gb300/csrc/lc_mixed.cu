@@ -206,7 +206,8 @@ __global__ void k_build_embedding(const double* __restrict__ V, int ldv, int r0,
 
 // ordered list of candidates with hn2 > eta2 (one CTA of 1024 threads)
 __global__ void __launch_bounds__(1024) k_compact_nonzero(const float* __restrict__ hn2, int count, float eta2,
-                                                          int* __restrict__ nz_idx, int* __restrict__ nnz) {
+                                                          int* __restrict__ nz_idx, int* __restrict__ nnz,
+                                                          const double* __restrict__ bn2, long long t0) {
   __shared__ int wsum[32];
   __shared__ int base;
   if (threadIdx.x == 0) base = 0;
@@ -214,7 +215,16 @@ __global__ void __launch_bounds__(1024) k_compact_nonzero(const float* __restric
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int c0 = 0; c0 < count; c0 += 1024) {
     const int c = c0 + threadIdx.x;
-    const int f = (c < count && hn2[c] > eta2) ? 1 : 0;
+    int f = 0;
+    if (c < count) {
+      float floor2 = eta2;
+      if (bn2) {
+        int l, m;
+        pair_from_index(t0 + c, &l, &m);
+        floor2 = (float)((double)eta2 * bn2[l] * bn2[m]);
+      }
+      f = hn2[c] > floor2 ? 1 : 0;
+    }
     const unsigned mask = __ballot_sync(0xffffffffu, f);
     const int pre = __popc(mask & ((1u << lane) - 1u));
     if (lane == 0) wsum[w] = __popc(mask);
@@ -267,8 +277,9 @@ cudaError_t build_embedding(const double* V, int ldv, int r0, int r1, int d, __n
   return cudaGetLastError();
 }
 
-cudaError_t compact_nonzero(const float* hn2, int count, float eta2, int* nz_idx, int* nnz, cudaStream_t s) {
-  k_compact_nonzero<<<1, 1024, 0, s>>>(hn2, count, eta2, nz_idx, nnz);
+cudaError_t compact_nonzero(const float* hn2, int count, float eta2, int* nz_idx, int* nnz, cudaStream_t s,
+                            const double* bn2, long long t0) {
+  k_compact_nonzero<<<1, 1024, 0, s>>>(hn2, count, eta2, nz_idx, nnz, bn2, t0);
   return cudaGetLastError();
 }
 
