@@ -195,6 +195,33 @@ LC_API int lie_closure_alg3_dev(const lc_c128* generators, int k, int d, double 
                          void* stream);
 
 /*
+ * lie_closure_resume -- continue Algorithm 4 from a saved state.  The state of
+ * Algorithm 4 is its basis V and its pair cursor (l, m) (Section 3.2): a call
+ * stopped by opt->max_candidates (or LC_ERR_CAPACITY) returns both, the basis
+ * in basis_out and the cursor in rep->cursor_l / rep->cursor_m.  Passing them
+ * back here runs the rest of the sweep; a run split this way gives the same
+ * basis as one uninterrupted run.
+ *
+ * basis_in : n_in x d x d complex128 host array, the orthonormal basis a
+ *            previous call returned (in its order); read only.
+ * cursor_l, cursor_m : the next pair, 0 <= cursor_m < cursor_l.
+ * max_dim  : capacity (>= n_in) of basis_out and of the device basis.
+ * basis_out, dim_out, opt, rep, return value: as lie_closure; basis_out
+ *            receives the whole basis (the n_in given elements first).
+ */
+LC_API int lie_closure_resume(const lc_c128* basis_in, long long n_in, long long cursor_l,
+                       long long cursor_m, int d, double tol, lc_c128* basis_out,
+                       long long* dim_out, long long max_dim, const lc_options* opt,
+                       lc_report* rep);
+
+/* lie_closure_resume_dev -- as lie_closure_resume with device buffers and a
+ * stream (conventions of lie_closure_dev). */
+LC_API int lie_closure_resume_dev(const lc_c128* basis_in, long long n_in, long long cursor_l,
+                           long long cursor_m, int d, double tol, lc_c128* basis_out,
+                           long long* dim_out, long long max_dim, const lc_options* opt,
+                           lc_report* rep, void* stream);
+
+/*
  * lie_closure_batched -- Algorithm 4 on nsets independent generator sets
  * (Section 3.2 applied per set), host buffers.
  *

@@ -32,8 +32,8 @@ PRECISIONS = {"fp64": LC_PREC_FP64, "mixed": LC_PREC_MIXED_BF16X3}
 
 # every symbol the public headers declare
 EXPORTED = ["lc_default_options", "lc_status_string", "lc_version", "lie_closure", "lie_closure_dev",
-            "lie_closure_batched", "lie_closure_alg3", "lie_closure_alg3_dev", "lc_split_gemm_f32",
-            "lc_split_gemm_f32_noalloc"]
+            "lie_closure_batched", "lie_closure_alg3", "lie_closure_alg3_dev", "lie_closure_resume",
+            "lie_closure_resume_dev", "lc_split_gemm_f32", "lc_split_gemm_f32_noalloc"]
 
 
 class LibraryNotBuilt(RuntimeError):
@@ -108,6 +108,12 @@ def lib():
         L.lie_closure_alg3.restype = ctypes.c_int
         L.lie_closure_alg3_dev.argtypes = L.lie_closure_alg3.argtypes + [c_p]
         L.lie_closure_alg3_dev.restype = ctypes.c_int
+        L.lie_closure_resume.argtypes = [c_p, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_int,
+                                         ctypes.c_double, c_p, ctypes.POINTER(ctypes.c_longlong), ctypes.c_longlong,
+                                         ctypes.POINTER(Options), ctypes.POINTER(Report)]
+        L.lie_closure_resume.restype = ctypes.c_int
+        L.lie_closure_resume_dev.argtypes = L.lie_closure_resume.argtypes + [c_p]
+        L.lie_closure_resume_dev.restype = ctypes.c_int
         L.lc_split_gemm_f32.argtypes = [c_p, c_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_p, c_p]
         L.lc_split_gemm_f32.restype = ctypes.c_int
         L.lc_split_gemm_f32_noalloc.argtypes = L.lc_split_gemm_f32.argtypes
@@ -165,6 +171,23 @@ def lie_closure(generators, tol: float, max_dim: int | None = None, return_basis
     _check(st, check)
     n = int(dim.value)
     return ClosureResult(n, basis[:n] if basis is not None else None, st, rep.as_dict())
+
+
+def lie_closure_resume(basis, cursor, tol: float, max_dim: int | None = None, check: bool = True,
+                       precision="mixed", **opts) -> ClosureResult:
+    """Continue Algorithm 4 from (basis, (l, m)) returned by an earlier call."""
+    b = np.ascontiguousarray(basis, dtype=np.complex128)
+    n, d, _ = b.shape
+    cap = int(max_dim) if max_dim is not None else d * d
+    out = np.zeros((cap, d, d), dtype=np.complex128)
+    dim = ctypes.c_longlong(0)
+    rep = Report()
+    o = make_options(precision, **opts)
+    st = lib().lie_closure_resume(b.ctypes.data, n, int(cursor[0]), int(cursor[1]), d, float(tol), out.ctypes.data,
+                                  ctypes.byref(dim), cap, ctypes.byref(o), ctypes.byref(rep))
+    _check(st, check)
+    k = int(dim.value)
+    return ClosureResult(k, out[:k], st, rep.as_dict())
 
 
 def lie_closure_alg3(generators, tol: float, max_dim: int | None = None, check: bool = True,

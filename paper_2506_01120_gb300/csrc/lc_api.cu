@@ -131,12 +131,21 @@ class Closure {
     tc_bracket_ = mixed_ && (bracket_tc_supported(d) || big_bracket_);
   }
 
+  // Resume: d_gens holds n_resume orthonormal basis elements returned by an
+  // earlier call; the generator pass is skipped and the sweep continues at the
+  // pair index t_resume.
+  long long n_resume_ = -1, t_resume_ = 0;
+  void set_resume(long long n, long long t) {
+    n_resume_ = n;
+    t_resume_ = t;
+  }
+
   int run(const double2* d_gens, double2* d_basis_out, long long* dim_out, lc_report* rep,
           double2* d_nested_out = nullptr) {
     const double t_start = now_s();
     t_last_accept_ = 0.0;
     int rc = setup(d_gens);
-    if (rc == LC_OK) rc = generator_pass();
+    if (rc == LC_OK) rc = (n_resume_ >= 0) ? resume_state() : generator_pass();
     if (rc == LC_OK) rc = sweep();
     if (rc == LC_OK || rc == LC_ERR_CAPACITY) {
       if (d_basis_out && N_ > 0) {
@@ -457,6 +466,20 @@ class Closure {
     return rc;
   }
 
+  int resume_state() {
+    if (n_resume_ > ncap_) return LC_ERR_CAPACITY;
+    // the packed elements are already the basis rows
+    LC_TRY(cudaMemcpy2DAsync(V64_, sizeof(double) * ldp_, G64_, sizeof(double) * ldp_, sizeof(double) * P_,
+                             (size_t)n_resume_, cudaMemcpyDeviceToDevice, s_));
+    if (mixed_ && n_resume_ > 0) {
+      LC_TRY(split_rows(V64_, ldp_, 0, (int)n_resume_, P_, Vhi_, Vlo_, ldp_, VThi_, VTlo_, ncap_pad_, s_));
+      if (tc_bracket_) LC_TRY(build_embedding(src(), ldp_, 0, (int)n_resume_, d_, Ehi_, Elo_, s_, big_bracket_ ? 1 : 0));
+      launches_ += 2;
+    }
+    N_ = n_resume_;
+    return LC_OK;
+  }
+
   int generator_pass() {
     LC_TRY(cudaMemcpy2DAsync(R64_, sizeof(double) * ldp_, G64_, sizeof(double) * ldp_, sizeof(double) * P_, k_,
                              cudaMemcpyDeviceToDevice, s_));
@@ -596,7 +619,7 @@ class Closure {
   // block appends nothing.  Any partition of the pair order gives the same
   // result.
   int sweep() {
-    t_ = 0;
+    t_ = n_resume_ >= 0 ? t_resume_ : 0;
     long long knext = Kgrow_;
     for (;;) {
       const long long T = pairs_below(N_);
@@ -631,9 +654,10 @@ int check_args(const void* g, int k, int d, double tol, long long max_dim, const
 
 int closure_device(const double2* d_gens, int k, int d, double tol, double2* d_basis, long long* dim_out,
                    long long max_dim, const lc_options& o, lc_report* rep, cudaStream_t s, bool alg3 = false,
-                   double2* d_nested = nullptr) {
+                   double2* d_nested = nullptr, long long resume_t = -1) {
   const long long ncap = std::min<long long>(max_dim, (long long)d * d);
   Closure c(k, d, tol, ncap, o, s, alg3);
+  if (resume_t >= 0) c.set_resume(k, resume_t);
   int rc = c.run(d_gens, d_basis, dim_out, rep, d_nested);
   if (rc == LC_OK && max_dim < (long long)d * d && dim_out && *dim_out > max_dim) rc = LC_ERR_CAPACITY;
   return rc;
@@ -643,7 +667,7 @@ int closure_device(const double2* d_gens, int k, int d, double tol, double2* d_b
 // copied out), used by lie_closure and by each batched worker.
 int closure_host(const lc_c128* generators, int k, int d, double tol, lc_c128* basis_out, long long* dim_out,
                  long long max_dim, const lc_options& o, lc_report* rep, cudaStream_t s, bool alg3 = false,
-                 lc_c128* nested_out = nullptr) {
+                 lc_c128* nested_out = nullptr, long long resume_t = -1) {
   if (dim_out) *dim_out = 0;
   int rc = check_args(generators, k, d, tol, max_dim, o);
   if (rc != LC_OK) return rc;
@@ -665,7 +689,7 @@ int closure_host(const lc_c128* generators, int k, int d, double tol, lc_c128* b
   if (rc == LC_OK && cudaMemcpyAsync(dg, generators, gbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
     rc = LC_ERR_CUDA;
   long long dim = 0;
-  if (rc == LC_OK) rc = closure_device(dg, k, d, tol, db, &dim, max_dim, o, rep, s, alg3, dn);
+  if (rc == LC_OK) rc = closure_device(dg, k, d, tol, db, &dim, max_dim, o, rep, s, alg3, dn, resume_t);
   if ((rc == LC_OK || rc == LC_ERR_CAPACITY) && dim > 0) {
     const size_t out = sizeof(double2) * (size_t)std::min(dim, ncap) * d * d;
     if (db && cudaMemcpyAsync(basis_out, db, out, cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = LC_ERR_CUDA;
@@ -810,6 +834,49 @@ int lie_closure_alg3_dev(const lc_c128* generators, int k, int d, double tol, lc
   return closure_device(reinterpret_cast<const double2*>(generators), k, d, tol,
                         reinterpret_cast<double2*>(basis_out), dim_out, max_dim, o, rep,
                         static_cast<cudaStream_t>(stream), true, reinterpret_cast<double2*>(nested_out));
+}
+
+namespace {
+int resume_args(const lc_c128* basis_in, long long n_in, long long l, long long m, int d, double tol,
+                long long max_dim, const lc_options& o, long long* t) {
+  if (!basis_in || n_in < 1 || n_in > (1ll << 30)) return LC_ERR_ARG;
+  if (l < 1 || m < 0 || m >= l) return LC_ERR_ARG;
+  if (max_dim < n_in) return LC_ERR_CAPACITY;
+  int rc = check_args(basis_in, (int)n_in, d, tol, max_dim, o);
+  if (rc != LC_OK) return rc;
+  *t = l * (l - 1) / 2 + m;
+  return LC_OK;
+}
+}  // namespace
+
+int lie_closure_resume(const lc_c128* basis_in, long long n_in, long long cursor_l, long long cursor_m, int d,
+                       double tol, lc_c128* basis_out, long long* dim_out, long long max_dim, const lc_options* opt,
+                       lc_report* rep) {
+  lc_options o;
+  if (opt) o = *opt; else lc_default_options(&o);
+  if (dim_out) *dim_out = 0;
+  long long t = 0;
+  int rc = resume_args(basis_in, n_in, cursor_l, cursor_m, d, tol, max_dim, o, &t);
+  if (rc != LC_OK) return rc;
+  cudaStream_t s;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return LC_ERR_CUDA;
+  rc = closure_host(basis_in, (int)n_in, d, tol, basis_out, dim_out, max_dim, o, rep, s, false, nullptr, t);
+  cudaStreamDestroy(s);
+  return rc;
+}
+
+int lie_closure_resume_dev(const lc_c128* basis_in, long long n_in, long long cursor_l, long long cursor_m, int d,
+                           double tol, lc_c128* basis_out, long long* dim_out, long long max_dim,
+                           const lc_options* opt, lc_report* rep, void* stream) {
+  lc_options o;
+  if (opt) o = *opt; else lc_default_options(&o);
+  if (dim_out) *dim_out = 0;
+  long long t = 0;
+  int rc = resume_args(basis_in, n_in, cursor_l, cursor_m, d, tol, max_dim, o, &t);
+  if (rc != LC_OK) return rc;
+  return closure_device(reinterpret_cast<const double2*>(basis_in), (int)n_in, d, tol,
+                        reinterpret_cast<double2*>(basis_out), dim_out, max_dim, o, rep,
+                        static_cast<cudaStream_t>(stream), false, nullptr, t);
 }
 
 int lie_closure_batched(int nsets, const lc_c128* const* generators, const int* k, const int* d, double tol,

@@ -213,3 +213,22 @@ def test_forced_wait_timeout_is_reported_and_device_stays_usable():
         assert r.status == binding.LC_ERR_TIMEOUT
         ok = binding.lie_closure(g, 1e-10, precision=prec)
         assert ok.status == binding.LC_OK and ok.dim == 63
+
+
+# ------------------------------------------------------------ checkpoint / resume
+@pytest.mark.parametrize("prec", PRECS)
+def test_resume_equals_uninterrupted_run(prec):
+    """Algorithm 4's state is (V, l, m): a run stopped after a prefix of the
+    sweep and resumed from its returned basis and cursor gives the same basis as
+    one run, and matches the oracle's resumed run."""
+    for g, tol, cut in [(inputs.generators_from_labels(inputs.su2n_chain_labels(3)), 1e-10, 700),
+                        (inputs.random_set(8, 2, seed=71), 1e-8, 150)]:
+        full = binding.lie_closure(g, tol, precision=prec)
+        part = binding.lie_closure(g, tol, precision=prec, max_candidates=cut)
+        cur = (part.report["cursor_l"], part.report["cursor_m"])
+        rest = binding.lie_closure_resume(part.basis, cur, tol, precision=prec)
+        assert rest.dim == full.dim
+        np.testing.assert_allclose(rest.basis, full.basis, atol=1e-12)
+        ref = oc.alg4_orthonormalization(g, tol, max_candidates=cut)
+        assert (ref.l, ref.m) == cur
+        np.testing.assert_allclose(rest.basis, oc.alg4_orthonormalization(g, tol, resume=ref).basis, atol=1e-11)
