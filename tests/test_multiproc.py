@@ -62,3 +62,60 @@ def test_reference_arm_under_torchrun_world2():
     assert j["impl"] == "reference" and j["n_gpus"] == 2 and j["value"] > 0
     assert j["cpu_baseline"]["kind"] == "oracle"
     assert j["e2e"]["h2d_bytes_per_step"] == 0
+
+
+# ------------------------------------------------- batched sets across ranks
+def test_lpt_assignment_balances_and_covers():
+    from paper_2506_01120_gb300 import shard
+    costs = [shard.set_cost(d, k) for d, k in [(64, 2), (64, 6), (32, 3), (16, 2), (8, 5), (64, 4), (8, 2)]]
+    for world in (1, 2, 3, 4):
+        shares = shard.assign(costs, world)
+        flat = sorted(i for s in shares for i in s)
+        assert flat == list(range(len(costs)))
+        loads = [sum(costs[i] for i in s) for s in shares]
+        # LPT bound: max load <= (4/3 - 1/(3 m)) OPT, and OPT >= max(mean, largest)
+        opt_lb = max(sum(costs) / world, max(costs))
+        assert max(loads) <= (4 / 3) * opt_lb + 1e-9
+    assert shard.assign(costs, 2) == shard.assign(list(costs), 2)     # deterministic
+
+
+def _shard_worker(rank, world, port, q):
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import torch.distributed as dist
+    from paper_2506_01120_gb300 import inputs, shard
+    dist.init_process_group("gloo")
+    sets = [s["generators"] for s in inputs.batched_sets(12, seed=5, dims=(8, 16))]
+
+    def fake_closure(gs, tol, **opts):
+        # stands in for the GPU call: one deterministic number per set
+        return [int(g.shape[1] * 100 + g.shape[0]) for g in gs], [0] * len(gs)
+
+    def gather(obj):
+        out = [None] * world
+        dist.all_gather_object(out, obj)
+        return out
+
+    dims, stats = shard.run_sharded(sets, 1e-8, rank, world, fake_closure, gather)
+    q.put((rank, dims, stats))
+    dist.destroy_process_group()
+
+
+def test_run_sharded_gathers_every_set_gloo():
+    import torch.multiprocessing as mp
+    from paper_2506_01120_gb300 import inputs
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(2))
+    sets = [s["generators"] for s in inputs.batched_sets(12, seed=5, dims=(8, 16))]
+    want = [int(g.shape[1] * 100 + g.shape[0]) for g in sets]
+    for rank, dims, stats in res:
+        assert dims == want and stats == [0] * 12
