@@ -145,14 +145,18 @@ def measured_peaks():
 def profiled_traffic(version: str):
     """DRAM bytes per launch of the screening GEMM from the committed ncu
     summary, if it was taken on this kernel version; else None."""
-    p = os.path.join(ROOT, "profiles", "split_gemm_traffic.json")
+    p = os.path.join(ROOT, "profiles", "split_gemm_traffic.txt")
     if not os.path.exists(p):
         return None
+    kv = {}
     with open(p) as fh:
-        j = json.load(fh)
-    if j.get("library_version") != version:
+        for line in fh:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+    if kv.get("library_version") != version:
         return None
-    return j.get("dram_bytes_per_launch")
+    return int(kv["dram_bytes_per_launch"])
 
 
 # ------------------------------------------------------------ CPU oracle leg
