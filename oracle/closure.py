@@ -16,6 +16,8 @@ Functions and the passage each follows
                       the Corollary and the equation after it).
 * ``alg4_orthonormalization`` -- Algorithm 4 (dimension-only orthonormalisation
                       method), O1.
+* ``alg2_matrix_inversion`` -- Algorithm 2 (the matrix-inversion method of
+                      Section 3.1: unit-norm B, Gram matrix A and its inverse).
 * ``alg3_orthonormalization`` -- Algorithm 3 (orthonormalisation keeping the
                       generators and nested brackets B beside V).
 * ``alg1_rank``    -- Algorithm 1 with the independence test done by matrix rank
@@ -200,6 +202,81 @@ def alg4_orthonormalization(generators: np.ndarray, tol: float, eta_abs: float =
     res.dim = n
     res.l, res.m = l, m
     res.t_total += time.perf_counter() - t0
+    return res
+
+
+# ------------------------------------------------------------- Algorithm 2
+@dataclass
+class Alg2Result:
+    B: np.ndarray          # (dim, d, d): unit-norm generators and nested brackets
+    A_inv: np.ndarray      # (dim, dim): inverse of the Gram matrix A_ij = <B_i, B_j>
+    dim: int
+    candidates: int = 0
+    residuals: list = field(default_factory=list)   # ||h - B (A^-1 beta)|| of accepts
+
+
+def alg2_matrix_inversion(generators: np.ndarray, tol: float, eta_abs: float = 1e-12,
+                          saturation_exit: bool = False) -> Alg2Result:
+    """Algorithm 2: the matrix-inversion method (Section 3.1, Theorem 1).
+
+    Operators enter B unit-normalised.  A candidate h (normalised) with
+    beta_i = <B_i, h> is independent iff h - sum_i B_i (A^-1 beta)_i != 0, read
+    as: its norm exceeds tol (h has unit norm, so this is the relative test);
+    brackets with ||[B_l, B_m]|| <= eta_abs are zero.  On accept A grows by the
+    row beta (A_{i,new} = beta_i, A_{new,i} = conj(beta_i), A_{new,new} = 1) and
+    A^-1 is recomputed.  Brackets are formed from B.
+    """
+    k, d, _ = generators.shape
+    cap = 2 * d * d
+    B = np.zeros((min(cap, 64), d, d), dtype=np.complex128)
+    A = np.zeros((0, 0), dtype=np.complex128)
+    A_inv = np.zeros((0, 0), dtype=np.complex128)
+    n = 0
+    res = Alg2Result(B=B, A_inv=A_inv, dim=0)
+
+    def try_append(h):
+        nonlocal B, A, A_inv, n
+        res.candidates += 1
+        hn = norm(h)
+        if hn <= eta_abs:
+            return
+        hb = h / hn
+        beta = coefficients(B[:n], hb) if n else np.zeros(0, dtype=np.complex128)
+        x = A_inv @ beta
+        r = hb - np.einsum("l,ljk->jk", x, B[:n]) if n else hb
+        rn = norm(r)
+        if rn <= tol:
+            return
+        if n >= cap:
+            raise CapacityError("closure dimension would exceed 2 d^2")
+        if n == B.shape[0]:
+            grown = np.zeros((max(4, 2 * n), d, d), dtype=np.complex128)
+            grown[:n] = B[:n]
+            B = grown
+        B[n] = hb
+        A_new = np.zeros((n + 1, n + 1), dtype=np.complex128)
+        A_new[:n, :n] = A
+        A_new[:n, n] = beta
+        A_new[n, :n] = beta.conj()
+        A_new[n, n] = 1.0
+        A = A_new
+        A_inv = np.linalg.inv(A)
+        res.residuals.append(rn)
+        n += 1
+
+    for g in generators:
+        try_append(np.asarray(g, dtype=np.complex128))
+    bound = max_dim_bound(generators) if saturation_exit else None
+    l, m = 1, 0
+    while l < n:
+        if bound is not None and n >= bound:
+            break
+        try_append(bracket(B[l], B[m]))
+        m += 1
+        if m == l:
+            l += 1
+            m = 0
+    res.B, res.A_inv, res.dim = B[:n], A_inv, n
     return res
 
 

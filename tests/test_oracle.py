@@ -289,3 +289,33 @@ def test_alg3_same_algebra_as_alg4(case):
         else:
             l, m = par
             np.testing.assert_array_equal(r3.B[i], oc.bracket(r3.B[l], r3.B[m]))
+
+
+# ------------------------------------------------------------- Algorithm 2
+@pytest.mark.parametrize("case", ["so6", "su8", "rand_d4", "pauli", "dependent"])
+def test_alg2_same_algebra(case):
+    """The matrix-inversion method (Theorem 1: h is dependent iff
+    h - B A^-1 beta = 0) finds the same algebra as Algorithm 4; B is unit-norm,
+    its Gram matrix times the stored inverse is the identity, and B's elements
+    after the generators are normalised brackets of earlier ones."""
+    if case == "so6":
+        g = inputs.generators_from_labels(inputs.so2n_chain_labels(3)); expect = 15
+    elif case == "su8":
+        g = inputs.generators_from_labels(inputs.su2n_chain_labels(3)); expect = 63
+    elif case == "rand_d4":
+        g = inputs.random_set(4, 2, seed=3); expect = 15
+    elif case == "pauli":
+        rng = np.random.default_rng(9)
+        labels = inputs.random_pauli_labels(3, 4, rng)
+        g = inputs.generators_from_labels(labels); expect = len(oc.pauli_closure(labels))
+    else:
+        a, b = inputs.generators_from_labels(["XX", "ZZ"])
+        g = np.stack([a, b, 0.3 * a - 2 * b]); expect = 2      # commuting, third dependent
+    r2 = oc.alg2_matrix_inversion(g, 1e-10)
+    r4 = oc.alg4_orthonormalization(g, 1e-10)
+    assert r2.dim == r4.dim == expect
+    assert oc.span_distance(r4.basis, r2.B) < 1e-9
+    for b in r2.B:
+        assert oc.norm(b) == pytest.approx(1.0, abs=1e-13)
+    G = oc.gram(r2.B)
+    assert np.max(np.abs(G @ r2.A_inv - np.eye(r2.dim))) < 1e-8
