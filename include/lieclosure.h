@@ -169,6 +169,30 @@ LC_API int lie_closure_dev(const lc_c128* generators, int k, int d, double tol,
                     const lc_options* opt, lc_report* rep, void* stream);
 
 /*
+ * lie_closure_alg2 -- Algorithm 2 of the paper (Section 3.1): the
+ * matrix-inversion method.  B holds unit-norm operators (the normalised
+ * generators and normalised brackets [B[l], B[m]], same pair order as
+ * lie_closure); a candidate h (normalised) is independent iff
+ * ||h - B^T (A^-1 beta)|| > tol, beta_i = <B_i, h>, with A the Gram matrix of B
+ * (Theorem 1).  A^-1 is kept and grown by the bordered-inverse identity on each
+ * append.  FP64 throughout (opt->precision is ignored).  The paper notes that
+ * A can become ill-conditioned; lie_closure (Algorithm 4) is the stable method.
+ *
+ * basis_out : host buffer for max_dim x d x d complex128 receiving B (unit
+ *             norm, not orthogonal), or NULL.  Other arguments as lie_closure;
+ *             max_dim also sizes the stored max_dim x max_dim inverse.
+ */
+LC_API int lie_closure_alg2(const lc_c128* generators, int k, int d, double tol,
+                     lc_c128* basis_out, long long* dim_out, long long max_dim,
+                     const lc_options* opt, lc_report* rep);
+
+/* lie_closure_alg2_dev -- as lie_closure_alg2 with device buffers and a stream
+ * (conventions of lie_closure_dev). */
+LC_API int lie_closure_alg2_dev(const lc_c128* generators, int k, int d, double tol,
+                         lc_c128* basis_out, long long* dim_out, long long max_dim,
+                         const lc_options* opt, lc_report* rep, void* stream);
+
+/*
  * lie_closure_alg3 -- Algorithm 3 of the paper (Section 3.2): the
  * orthonormalisation method that keeps, beside the orthonormal basis V, the
  * basis B made of the accepted generators and nested brackets themselves.

@@ -32,7 +32,8 @@ PRECISIONS = {"fp64": LC_PREC_FP64, "mixed": LC_PREC_MIXED_BF16X3}
 
 # every symbol the public headers declare
 EXPORTED = ["lc_default_options", "lc_status_string", "lc_version", "lie_closure", "lie_closure_dev",
-            "lie_closure_batched", "lie_closure_alg3", "lie_closure_alg3_dev", "lie_closure_resume",
+            "lie_closure_batched", "lie_closure_alg2", "lie_closure_alg2_dev", "lie_closure_alg3",
+            "lie_closure_alg3_dev", "lie_closure_resume",
             "lie_closure_resume_dev", "lc_split_gemm_f32", "lc_split_gemm_f32_noalloc"]
 
 
@@ -102,6 +103,10 @@ def lib():
                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Options),
                                           ctypes.POINTER(Report)]
         L.lie_closure_batched.restype = ctypes.c_int
+        L.lie_closure_alg2.argtypes = L.lie_closure.argtypes
+        L.lie_closure_alg2.restype = ctypes.c_int
+        L.lie_closure_alg2_dev.argtypes = L.lie_closure_dev.argtypes
+        L.lie_closure_alg2_dev.restype = ctypes.c_int
         L.lie_closure_alg3.argtypes = [c_p, ctypes.c_int, ctypes.c_int, ctypes.c_double, c_p, c_p,
                                        ctypes.POINTER(ctypes.c_longlong), ctypes.c_longlong,
                                        ctypes.POINTER(Options), ctypes.POINTER(Report)]
@@ -171,6 +176,25 @@ def lie_closure(generators, tol: float, max_dim: int | None = None, return_basis
     _check(st, check)
     n = int(dim.value)
     return ClosureResult(n, basis[:n] if basis is not None else None, st, rep.as_dict())
+
+
+def lie_closure_alg2(generators, tol: float, max_dim: int | None = None, check: bool = True,
+                     **opts) -> ClosureResult:
+    """Algorithm 2 (matrix-inversion method) on host arrays; basis = unit-norm B."""
+    g = np.ascontiguousarray(generators, dtype=np.complex128)
+    if g.ndim != 3 or g.shape[1] != g.shape[2]:
+        raise ValueError("generators must have shape (k, d, d)")
+    k, d, _ = g.shape
+    cap = int(max_dim) if max_dim is not None else d * d
+    basis = np.zeros((cap, d, d), dtype=np.complex128)
+    dim = ctypes.c_longlong(0)
+    rep = Report()
+    o = make_options("fp64", **opts)
+    st = lib().lie_closure_alg2(g.ctypes.data, k, d, float(tol), basis.ctypes.data, ctypes.byref(dim), cap,
+                                ctypes.byref(o), ctypes.byref(rep))
+    _check(st, check)
+    n = int(dim.value)
+    return ClosureResult(n, basis[:n], st, rep.as_dict())
 
 
 def lie_closure_resume(basis, cursor, tol: float, max_dim: int | None = None, check: bool = True,

@@ -836,6 +836,51 @@ int lie_closure_alg3_dev(const lc_c128* generators, int k, int d, double tol, lc
                         static_cast<cudaStream_t>(stream), true, reinterpret_cast<double2*>(nested_out));
 }
 
+int lie_closure_alg2_dev(const lc_c128* generators, int k, int d, double tol, lc_c128* basis_out,
+                         long long* dim_out, long long max_dim, const lc_options* opt, lc_report* rep,
+                         void* stream) {
+  lc_options o;
+  if (opt) o = *opt; else lc_default_options(&o);
+  if (dim_out) *dim_out = 0;
+  int rc = check_args(generators, k, d, tol, max_dim, o);
+  if (rc != LC_OK) return rc;
+  return closure_alg2_device(reinterpret_cast<const double2*>(generators), k, d, tol,
+                             reinterpret_cast<double2*>(basis_out), dim_out, max_dim, o, rep,
+                             static_cast<cudaStream_t>(stream));
+}
+
+int lie_closure_alg2(const lc_c128* generators, int k, int d, double tol, lc_c128* basis_out, long long* dim_out,
+                     long long max_dim, const lc_options* opt, lc_report* rep) {
+  lc_options o;
+  if (opt) o = *opt; else lc_default_options(&o);
+  if (dim_out) *dim_out = 0;
+  int rc = check_args(generators, k, d, tol, max_dim, o);
+  if (rc != LC_OK) return rc;
+  cudaStream_t s;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return LC_ERR_CUDA;
+  const size_t gbytes = sizeof(double2) * (size_t)k * d * d;
+  const long long ncap = std::min<long long>(max_dim, (long long)d * d);
+  const size_t bbytes = basis_out ? sizeof(double2) * (size_t)ncap * d * d : 0;
+  double2 *dg = nullptr, *db = nullptr;
+  long long dim = 0;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&dg), gbytes, s) != cudaSuccess) rc = LC_ERR_OOM;
+  if (rc == LC_OK && bbytes && cudaMallocAsync(reinterpret_cast<void**>(&db), bbytes, s) != cudaSuccess)
+    rc = LC_ERR_OOM;
+  if (rc == LC_OK && cudaMemcpyAsync(dg, generators, gbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    rc = LC_ERR_CUDA;
+  if (rc == LC_OK) rc = closure_alg2_device(dg, k, d, tol, db, &dim, max_dim, o, rep, s);
+  if ((rc == LC_OK || rc == LC_ERR_CAPACITY) && db && dim > 0 &&
+      cudaMemcpyAsync(basis_out, db, sizeof(double2) * (size_t)std::min(dim, ncap) * d * d,
+                      cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    rc = LC_ERR_CUDA;
+  if (dg) cudaFreeAsync(dg, s);
+  if (db) cudaFreeAsync(db, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && rc == LC_OK) rc = LC_ERR_CUDA;
+  cudaStreamDestroy(s);
+  if (dim_out) *dim_out = dim;
+  return rc;
+}
+
 namespace {
 int resume_args(const lc_c128* basis_in, long long n_in, long long l, long long m, int d, double tol,
                 long long max_dim, const lc_options& o, long long* t) {

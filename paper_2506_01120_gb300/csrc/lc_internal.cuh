@@ -150,6 +150,10 @@ cudaError_t bracket_big(const __nv_bfloat16* Ehi, const __nv_bfloat16* Elo, long
                         int count, __nv_bfloat16* Hhi, __nv_bfloat16* Hlo, int ldh, float* hn2, long long spin_cap,
                         DevStatus* st, cudaStream_t s);
 
+// Algorithm 2, the matrix-inversion method (lc_alg2.cu), FP64 throughout
+int closure_alg2_device(const double2* d_gens, int k, int d, double tol, double2* d_out, long long* dim_out,
+                        long long max_dim, const lc_options& o, lc_report* rep, cudaStream_t s);
+
 // tcgen05 split-BF16 GEMMs (lc_tcgen05.cu).  All operands K-major BF16.
 // D[M x N] = Ahi*Bhi^T + Ahi*Blo^T + Alo*Bhi^T with FP32 accumulation.
 struct SplitGemmArgs {
