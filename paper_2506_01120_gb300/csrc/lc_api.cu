@@ -129,6 +129,7 @@ class Closure {
     eta_screen_ = std::max(eta_, 1e-5);
     big_bracket_ = mixed_ && !bracket_tc_supported(d) && bracket_big_supported(d);
     tc_bracket_ = mixed_ && (bracket_tc_supported(d) || big_bracket_);
+    q_bracket_ = mixed_ && d == 64;      // [Hr; Hi] operands instead of the 2d x 2d embedding
   }
 
   // Resume: d_gens holds n_resume orthonormal basis elements returned by an
@@ -230,7 +231,7 @@ class Closure {
   __nv_bfloat16 *Chi_ = nullptr, *Clo_ = nullptr, *Ehi_ = nullptr, *Elo_ = nullptr;
   float *hn2f_ = nullptr, *rn2f_ = nullptr, *hn2c_ = nullptr;
   int *nz_idx_ = nullptr, *nnz_ = nullptr;
-  bool tc_bracket_ = false, big_bracket_ = false;
+  bool tc_bracket_ = false, big_bracket_ = false, q_bracket_ = false;
 
   void carve() {
     G64_ = ar_.take<double>((size_t)k_ * ldp_);
@@ -278,8 +279,9 @@ class Closure {
       nnz_ = ar_.take<int>(1);
       if (tc_bracket_) {
         const size_t R = 2 * (size_t)d_;
-        Ehi_ = ar_.take<__nv_bfloat16>((size_t)ncap_ * R * R);
-        Elo_ = ar_.take<__nv_bfloat16>((size_t)ncap_ * R * R);
+        const size_t per = q_bracket_ ? R * d_ : R * R;
+        Ehi_ = ar_.take<__nv_bfloat16>((size_t)ncap_ * per);
+        Elo_ = ar_.take<__nv_bfloat16>((size_t)ncap_ * per);
       }
     }
   }
@@ -457,7 +459,8 @@ class Closure {
       LC_TRY(split_rows(V64_, ldp_, n0, (int)n1, P_, Vhi_, Vlo_, ldp_, VThi_, VTlo_, ncap_pad_, s_));
       launches_ += 1;
       if (tc_bracket_) {
-        LC_TRY(build_embedding(src(), ldp_, n0, (int)n1, d_, Ehi_, Elo_, s_, big_bracket_ ? 1 : 0));
+        if (q_bracket_) LC_TRY(build_q(src(), ldp_, n0, (int)n1, d_, Ehi_, Elo_, s_));
+        else LC_TRY(build_embedding(src(), ldp_, n0, (int)n1, d_, Ehi_, Elo_, s_, big_bracket_ ? 1 : 0));
         launches_ += 1;
       }
       ph_end(PH_OTHER);
@@ -473,7 +476,9 @@ class Closure {
                              (size_t)n_resume_, cudaMemcpyDeviceToDevice, s_));
     if (mixed_ && n_resume_ > 0) {
       LC_TRY(split_rows(V64_, ldp_, 0, (int)n_resume_, P_, Vhi_, Vlo_, ldp_, VThi_, VTlo_, ncap_pad_, s_));
-      if (tc_bracket_) LC_TRY(build_embedding(src(), ldp_, 0, (int)n_resume_, d_, Ehi_, Elo_, s_, big_bracket_ ? 1 : 0));
+      if (q_bracket_) LC_TRY(build_q(src(), ldp_, 0, (int)n_resume_, d_, Ehi_, Elo_, s_));
+      else if (tc_bracket_)
+        LC_TRY(build_embedding(src(), ldp_, 0, (int)n_resume_, d_, Ehi_, Elo_, s_, big_bracket_ ? 1 : 0));
       launches_ += 2;
     }
     N_ = n_resume_;
@@ -544,7 +549,9 @@ class Closure {
 
   int block_mixed(long long t0, int kb) {
     ph_begin();
-    if (big_bracket_) {
+    if (q_bracket_) {
+      LC_TRY(bracket_q64(Ehi_, Elo_, ncap_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, opt.spin_cap, st_, s_));
+    } else if (big_bracket_) {
       LC_TRY(bracket_big(Ehi_, Elo_, ncap_, d_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, opt.spin_cap, st_, s_));
     } else if (tc_bracket_) {
       LC_TRY(bracket_tc(Ehi_, Elo_, ncap_, d_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, opt.spin_cap, st_, s_));

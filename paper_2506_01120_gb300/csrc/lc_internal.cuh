@@ -130,6 +130,13 @@ cudaError_t bracket_mixed(const double* V, int d, int ldv, long long t0, int cou
 // (perm: rows in the large-d bracket order, see lc_tcgen05.cu)
 cudaError_t build_embedding(const double* V, int ldv, int r0, int r1, int d, __nv_bfloat16* Ehi,
                             __nv_bfloat16* Elo, cudaStream_t s, int perm = 0);
+// [Hr; Hi] (2d x d, split BF16) of basis rows [r0, r1): operands of bracket_q64
+cudaError_t build_q(const double* V, int ldv, int r0, int r1, int d, __nv_bfloat16* Qhi, __nv_bfloat16* Qlo,
+                    cudaStream_t s);
+// tensor-core brackets for d = 64 from the [Hr; Hi] rows (nelems elements)
+cudaError_t bracket_q64(const __nv_bfloat16* Qhi, const __nv_bfloat16* Qlo, long long nelems, long long t0, int count,
+                        __nv_bfloat16* Hhi, __nv_bfloat16* Hlo, int ldh, float* hn2, long long spin_cap,
+                        DevStatus* st, cudaStream_t s);
 // ordered indices of the candidates with hn2 > eta2; their count to *nnz (device)
 // (bn2, optional: squared norms of the bracket operands' rows; the floor is
 // then eta2 * bn2[l] * bn2[m] for the pair t0 + position)

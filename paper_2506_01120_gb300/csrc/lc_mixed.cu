@@ -204,6 +204,30 @@ __global__ void k_build_embedding(const double* __restrict__ V, int ldv, int r0,
   }
 }
 
+// Q[i] = [Hr; Hi] (2d x d, split BF16) for basis rows i in [r0, r1)
+__global__ void k_build_q(const double* __restrict__ V, int ldv, int r0, int r1, int d,
+                          __nv_bfloat16* __restrict__ Qhi, __nv_bfloat16* __restrict__ Qlo) {
+  const long long per = 2LL * d * d;
+  const long long tot = per * (r1 - r0);
+  const double s1 = sqrt((double)d), s2 = sqrt((double)d / 2.0);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = r0 + e / per;
+    const int a = (int)((e / d) % (2 * d)), b = (int)(e % d);
+    const int ja = a % d;
+    const double* S = V + i * ldv;
+    double hr, hi;
+    if (ja == b)      { hr = S[(long long)ja * d + ja] * s1; hi = 0.0; }
+    else if (ja < b)  { hr = S[(long long)ja * d + b] * s2; hi = S[(long long)b * d + ja] * s2; }
+    else              { hr = S[(long long)b * d + ja] * s2; hi = -S[(long long)ja * d + b] * s2; }
+    __nv_bfloat16 h, lo;
+    split_bf16(a < d ? hr : hi, h, lo);
+    const long long o = i * per + (long long)a * d + b;
+    Qhi[o] = h;
+    Qlo[o] = lo;
+  }
+}
+
 // ordered list of candidates with hn2 > eta2 (one CTA of 1024 threads)
 __global__ void __launch_bounds__(1024) k_compact_nonzero(const float* __restrict__ hn2, int count, float eta2,
                                                           int* __restrict__ nz_idx, int* __restrict__ nnz,
@@ -274,6 +298,16 @@ cudaError_t build_embedding(const double* V, int ldv, int r0, int r1, int d, __n
   long long g = (tot + 255) / 256;
   if (g > 152 * 32) g = 152 * 32;
   k_build_embedding<<<(int)g, 256, 0, s>>>(V, ldv, r0, r1, d, perm, Ehi, Elo);
+  return cudaGetLastError();
+}
+
+cudaError_t build_q(const double* V, int ldv, int r0, int r1, int d, __nv_bfloat16* Qhi, __nv_bfloat16* Qlo,
+                    cudaStream_t s) {
+  if (r1 <= r0) return cudaSuccess;
+  const long long tot = 2LL * d * d * (r1 - r0);
+  long long g = (tot + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_build_q<<<(int)g, 256, 0, s>>>(V, ldv, r0, r1, d, Qhi, Qlo);
   return cudaGetLastError();
 }
 

@@ -54,6 +54,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -555,6 +559,9 @@ namespace {
 
 template <int D>
 struct BrCfg {
+  // MMA rows: the first D rows of E_l.  For D = 64 the M = 64 shape is used;
+  // its accumulator row i sits in TMEM lane 32 (i / 16) + i % 16.
+  static constexpr int MM = D == 64 ? 64 : 128;
   static constexpr int R = 2 * D;              // rows of E = MMA N = K extent
   static constexpr int TILE = R * 64 * 2;       // one R x 64 BF16 tile
   static constexpr int STAGE = 4 * TILE;        // El hi/lo, Em hi/lo
@@ -617,7 +624,7 @@ __global__ void __launch_bounds__(128, 1)
     }
     if (issued > 0) mbar_wait_bounded(&full_bar, (uint32_t)(issued - 1) & 1u, kDrainNs);
   } else if (warp == 1 && lane == 0) {
-    constexpr uint32_t idesc = make_idesc_bf16(128, C::R);
+    constexpr uint32_t idesc = make_idesc_bf16(C::MM, C::R);
     constexpr uint32_t idesc_neg = idesc | (1u << 13);      // negate A
     for (int kc = 0; kc < C::NK; ++kc) {
       if (!mbar_wait_bounded(&full_bar, (uint32_t)kc & 1u, limit_ns)) {
@@ -653,9 +660,11 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   tc_fence_after();
   const bool run = !(*(volatile int*)&abort_flag);
-  const int j = warp * 32 + lane;                      // output row
+  // output row of this lane (M = 64: lanes 0-15 of each warp quarter)
+  const int j = C::MM == 64 ? warp * 16 + (lane & 15) : warp * 32 + lane;
+  const bool mine = C::MM == 64 ? lane < 16 : j < D;
   float ss = 0.f;
-  if (run && warp * 32 < D) {                          // warp-uniform
+  if (run && (C::MM == 64 || warp * 32 < D)) {         // warp-uniform
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
     const float s1 = rsqrtf((float)D), s2 = sqrtf(2.f / (float)D);
     __nv_bfloat16* oh = Hhi + (long long)pair * ldh + (long long)j * D;
@@ -664,6 +673,7 @@ __global__ void __launch_bounds__(128, 1)
       float re[32], im[32];
       tmem_ld_32cols(trow + (uint32_t)c, re);
       tmem_ld_32cols(trow + (uint32_t)(D + c), im);
+      if (!mine) continue;
       __align__(16) __nv_bfloat16 hi[32], lo[32];
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
@@ -814,6 +824,171 @@ extern "C" LC_API int lc_split_gemm_f32_noalloc(const float* A, const float* B, 
   if (rc == LC_OK && hst.code != 0) rc = hst.code;
   return rc;
 }
+
+// ------------------------------------------- d = 64 brackets from [Hr; Hi]
+// Each basis element is also stored as P = [Hr; Hi] (2d x d rows, split
+// BF16): half the bytes of the 2d x 2d embedding.  With A = H_l, B = H_m and
+// the tcgen05 product MMA(X, Y) = X Y^T (both operands row-major d x d),
+// Hr^T = Hr and Hi^T = -Hi give
+//   Re(AB - BA) =  MMA(Ar, Br) + MMA(Ai, Bi) - MMA(Br, Ar) - MMA(Bi, Ai)
+//   Im(AB - BA) = -MMA(Ar, Bi) + MMA(Ai, Br) + MMA(Br, Ai) - MMA(Bi, Ar)
+// (each term three split MMAs; the minus signs use the negate-A bit), into two
+// 64-column TMEM accumulators.  M = 64 shape: row i in lane 32 (i/16) + i%16.
+namespace lc {
+namespace {
+
+constexpr int Q_D = 64;
+constexpr int Q_TILE = Q_D * Q_D * 2;          // one d x d BF16 tile (8 KB)
+constexpr int Q_STAGE = 8 * Q_TILE;           // Ar, Ai, Br, Bi in hi and lo
+constexpr int Q_SMEM = Q_STAGE + 1024;
+constexpr int Q_TMEM = 128;
+
+__global__ void __launch_bounds__(128, 1)
+    k_bracket_q64(const __grid_constant__ CUtensorMap mQhi, const __grid_constant__ CUtensorMap mQlo, long long t0,
+                  __nv_bfloat16* __restrict__ Hhi, __nv_bfloat16* __restrict__ Hlo, int ldh, float* __restrict__ hn2,
+                  uint64_t limit_ns, DevStatus* st) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar, done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  __shared__ float red[4];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pair = blockIdx.x;
+  int l, m;
+  pair_from_index(t0 + pair, &l, &m);
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  if (threadIdx.x == 0) {
+    mbar_init(&full_bar, 1);
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(Q_TMEM)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  // shared-memory tiles: [Ar Ai Br Bi] hi, then [Ar Ai Br Bi] lo
+  if (warp == 0 && lane == 0) {
+    mbar_expect_tx(&full_bar, Q_STAGE);
+    tma_load_2d(smem + 0 * Q_TILE, &mQhi, &full_bar, 0, l * 2 * Q_D);
+    tma_load_2d(smem + 1 * Q_TILE, &mQhi, &full_bar, 0, l * 2 * Q_D + Q_D);
+    tma_load_2d(smem + 2 * Q_TILE, &mQhi, &full_bar, 0, m * 2 * Q_D);
+    tma_load_2d(smem + 3 * Q_TILE, &mQhi, &full_bar, 0, m * 2 * Q_D + Q_D);
+    tma_load_2d(smem + 4 * Q_TILE, &mQlo, &full_bar, 0, l * 2 * Q_D);
+    tma_load_2d(smem + 5 * Q_TILE, &mQlo, &full_bar, 0, l * 2 * Q_D + Q_D);
+    tma_load_2d(smem + 6 * Q_TILE, &mQlo, &full_bar, 0, m * 2 * Q_D);
+    tma_load_2d(smem + 7 * Q_TILE, &mQlo, &full_bar, 0, m * 2 * Q_D + Q_D);
+    mbar_wait_bounded(&full_bar, 0u, kDrainNs);       // copies land before anything can leave
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t id = make_idesc_bf16(64, Q_D);
+    constexpr uint32_t idn = id | (1u << 13);        // negate A
+    if (!mbar_wait_bounded(&full_bar, 0u, limit_ns)) {
+      record_timeout(st, SITE_GEMM_MMA_WAIT, pair);
+      abort_flag = 1;
+    } else {
+      tc_fence_after();
+      const uint32_t base = smem_u32(smem);
+      const uint32_t ARh = base, AIh = base + Q_TILE, BRh = base + 2 * Q_TILE, BIh = base + 3 * Q_TILE;
+      const uint32_t lo = 4 * Q_TILE;
+      const uint32_t tre = tmem, tim = tmem + 64;
+      const uint32_t X[8] = {ARh, AIh, BRh, BIh, ARh, AIh, BRh, BIh};
+      const uint32_t Y[8] = {BRh, BIh, ARh, AIh, BIh, BRh, AIh, ARh};
+      const uint32_t NG[8] = {0, 0, 1, 1, 1, 0, 0, 1};
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const uint32_t dsc = NG[t] ? idn : id;
+        const uint32_t td = t < 4 ? tre : tim;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t off = kk * 32;
+          const uint64_t xh = make_sw128_desc(X[t] + off), xl = make_sw128_desc(X[t] + lo + off);
+          const uint64_t yh = make_sw128_desc(Y[t] + off), yl = make_sw128_desc(Y[t] + lo + off);
+          mma_bf16(td, xh, yh, dsc, ((t & 3) | kk) ? 1u : 0u);   // first product of each accumulator starts it
+          mma_bf16(td, xh, yl, dsc, 1u);
+          mma_bf16(td, xl, yh, dsc, 1u);
+        }
+      }
+    }
+    mma_commit(&done_bar);
+  }
+  __syncwarp();
+  const bool have = mbar_wait_bounded(&done_bar, 0u, limit_ns);
+  if (!have) {
+    record_timeout(st, SITE_GEMM_EPI_WAIT, pair);
+    atomicExch(&abort_flag, 1);
+    mbar_wait_bounded(&done_bar, 0u, kDrainNs);
+  }
+  __syncthreads();
+  tc_fence_after();
+  const bool run = !(*(volatile int*)&abort_flag);
+  const int j = warp * 16 + (lane & 15);               // M = 64: lanes 0-15 of each quarter
+  const bool mine = lane < 16;
+  float ss = 0.f;
+  if (run) {
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    const float s1 = rsqrtf((float)Q_D), s2 = sqrtf(2.f / (float)Q_D);
+    __nv_bfloat16* oh = Hhi + (long long)pair * ldh + (long long)j * Q_D;
+    __nv_bfloat16* ol = Hlo + (long long)pair * ldh + (long long)j * Q_D;
+    for (int c = 0; c < Q_D; c += 32) {
+      float re[32], im[32];
+      tmem_ld_32cols(trow + (uint32_t)c, re);
+      tmem_ld_32cols(trow + (uint32_t)(64 + c), im);
+      if (!mine) continue;
+      __align__(16) __nv_bfloat16 hi[32], lov[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int k = c + i;
+        const float v = (k > j) ? -s2 * im[i] : ((k == j) ? -s1 * im[i] : -s2 * re[i]);
+        ss = fmaf(v, v, ss);
+        hi[i] = __float2bfloat16_rn(v);
+        lov[i] = __float2bfloat16_rn(v - __bfloat162float(hi[i]));
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        reinterpret_cast<uint4*>(oh + c)[i] = reinterpret_cast<const uint4*>(hi)[i];
+        reinterpret_cast<uint4*>(ol + c)[i] = reinterpret_cast<const uint4*>(lov)[i];
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if (lane == 0) red[warp] = ss;
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && run) hn2[pair] = red[0] + red[1] + red[2] + red[3];
+  if (warp == 2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Q_TMEM) : "memory");
+  }
+}
+
+}  // namespace
+
+cudaError_t bracket_q64(const __nv_bfloat16* Qhi, const __nv_bfloat16* Qlo, long long nelems, long long t0, int count,
+                        __nv_bfloat16* Hhi, __nv_bfloat16* Hlo, int ldh, float* hn2, long long spin_cap,
+                        DevStatus* st, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  CUtensorMap mh, ml;
+  if (!make_map(&mh, Qhi, nelems * 2 * Q_D, Q_D, Q_D, Q_D) || !make_map(&ml, Qlo, nelems * 2 * Q_D, Q_D, Q_D, Q_D))
+    return cudaErrorInvalidValue;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(k_bracket_q64, cudaFuncAttributeMaxDynamicSharedMemorySize, Q_SMEM);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  const uint64_t lim = spin_cap > 0 ? (uint64_t)spin_cap : 4000000000ull;
+  k_bracket_q64<<<count, 128, Q_SMEM, s>>>(mh, ml, t0, Hhi, Hlo, ldh, hn2, lim, st);
+  return cudaGetLastError();
+}
+
+}  // namespace lc
 
 // --------------------------------------------------- large-d tensor brackets
 // For d >= 256 (d % 128 == 0) a bracket is a d x 2d x 2d real GEMM per term.
