@@ -262,6 +262,64 @@ LC_API int lie_closure_batched(int nsets, const lc_c128* const* generators, cons
                         const long long* max_dim, long long* dim_out, int* status_out,
                         const lc_options* opt, lc_report* rep);
 
+/*
+ * lie_closure_pauli -- Algorithm 4 (Section 3.2) on operators held as sparse
+ * sums of Pauli strings, the representation Section 3 recommends for large
+ * systems and Section 4.2 uses for Table 2.  No d x d matrix is formed.
+ *
+ * Representation.  An operator is a = i * sum_t c_t P_t with real c_t (so a is
+ * anti-Hermitian) and P_t an n-qubit Pauli string.  A string is packed into
+ * one 64-bit word as x | (z << 32): bit q of x / z is the X / Z part on qubit
+ * q+1 (qubit 1 is the leftmost Kronecker factor), so (x, z) = (1, 0) is X,
+ * (1, 1) is Y and (0, 1) is Z on that qubit.  Distinct strings are orthonormal
+ * under <a, b> = tr(a^dagger b) / d (Section 2.2), so <a, b> = sum_t a_t b_t
+ * over common strings and every step of the method is done on the coefficient
+ * lists: a bracket of two strings is zero when they commute and
+ * +-2i times the string x1^x2 | z1^z2 when they anticommute.
+ *
+ * strings, coefs : the generators' terms, concatenated; generator j owns
+ *              entries [offsets[j], offsets[j+1]).  Host memory, read only.
+ *              Repeated strings inside one generator are summed.
+ * offsets    : k + 1 non-decreasing entries, offsets[0] = 0.
+ * n_qubits   : 1 .. 31; every string must have no bit at or above n_qubits in
+ *              x or z (else LC_ERR_ARG).
+ * tol        : relative tolerance of the independence test (as lie_closure).
+ * basis_strings, basis_coefs : host buffers of term_capacity entries receiving
+ *              the orthonormal basis V in the order Algorithm 4 appends it,
+ *              each element's terms sorted by string; element i owns entries
+ *              [basis_offsets[i], basis_offsets[i+1]).  Terms whose magnitude
+ *              is below 1e-13 of the element's norm are dropped.  May be NULL
+ *              (dimension only).
+ * basis_offsets : host buffer of max_dim + 1 entries (or NULL).
+ * term_capacity : total terms the basis may hold (>= 1); sizes the device
+ *              arrays too.  Exceeding it returns LC_ERR_CAPACITY.
+ * max_dim    : capacity in elements (>= 1).
+ * opt, rep   : as lie_closure; opt->precision is ignored (everything is FP64,
+ *              exact for single-string sets), opt->block_k is the candidate
+ *              block (0 = 2^20), opt->fault_inject = 2 starts the per-candidate
+ *              hash tables at their smallest size (a test hook that exercises
+ *              the regrow path).
+ * Returns LC_OK, LC_ERR_ARG, LC_ERR_NONFINITE, LC_ERR_CAPACITY (basis,
+ * term or per-candidate hash capacity exceeded; *dim_out elements are valid),
+ * LC_ERR_CUDA or LC_ERR_OOM.
+ */
+LC_API int lie_closure_pauli(const unsigned long long* strings, const double* coefs,
+                      const long long* offsets, int k, int n_qubits, double tol,
+                      unsigned long long* basis_strings, double* basis_coefs,
+                      long long* basis_offsets, long long term_capacity,
+                      long long* dim_out, long long max_dim, const lc_options* opt,
+                      lc_report* rep);
+
+/* lie_closure_pauli_dev -- as lie_closure_pauli with every array (offsets
+ * included) in device memory of the current device and a stream (conventions
+ * of lie_closure_dev). */
+LC_API int lie_closure_pauli_dev(const unsigned long long* strings, const double* coefs,
+                          const long long* offsets, int k, int n_qubits, double tol,
+                          unsigned long long* basis_strings, double* basis_coefs,
+                          long long* basis_offsets, long long term_capacity,
+                          long long* dim_out, long long max_dim, const lc_options* opt,
+                          lc_report* rep, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,7 +34,8 @@ PRECISIONS = {"fp64": LC_PREC_FP64, "mixed": LC_PREC_MIXED_BF16X3}
 EXPORTED = ["lc_default_options", "lc_status_string", "lc_version", "lie_closure", "lie_closure_dev",
             "lie_closure_batched", "lie_closure_alg2", "lie_closure_alg2_dev", "lie_closure_alg3",
             "lie_closure_alg3_dev", "lie_closure_resume",
-            "lie_closure_resume_dev", "lc_split_gemm_f32", "lc_split_gemm_f32_noalloc"]
+            "lie_closure_resume_dev", "lie_closure_pauli", "lie_closure_pauli_dev", "lc_split_gemm_f32",
+            "lc_split_gemm_f32_noalloc"]
 
 
 class LibraryNotBuilt(RuntimeError):
@@ -119,6 +120,12 @@ def lib():
         L.lie_closure_resume.restype = ctypes.c_int
         L.lie_closure_resume_dev.argtypes = L.lie_closure_resume.argtypes + [c_p]
         L.lie_closure_resume_dev.restype = ctypes.c_int
+        L.lie_closure_pauli.argtypes = [c_p, c_p, c_p, ctypes.c_int, ctypes.c_int, ctypes.c_double, c_p, c_p, c_p,
+                                        ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong), ctypes.c_longlong,
+                                        ctypes.POINTER(Options), ctypes.POINTER(Report)]
+        L.lie_closure_pauli.restype = ctypes.c_int
+        L.lie_closure_pauli_dev.argtypes = L.lie_closure_pauli.argtypes + [c_p]
+        L.lie_closure_pauli_dev.restype = ctypes.c_int
         L.lc_split_gemm_f32.argtypes = [c_p, c_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_p, c_p]
         L.lc_split_gemm_f32.restype = ctypes.c_int
         L.lc_split_gemm_f32_noalloc.argtypes = L.lc_split_gemm_f32.argtypes
@@ -283,6 +290,79 @@ def lie_closure_batched(generator_sets, tol: float, max_dims=None, return_basis:
     dims_l = [int(x) for x in dims]
     out_b = [bases[i][:dims_l[i]] for i in range(n)] if bases is not None else None
     return dims_l, [int(x) for x in stat], out_b, [r.as_dict() for r in reps]
+
+
+@dataclass
+class PauliClosureResult:
+    """Basis of a Pauli-sum closure: element i is i * sum_t coefs[t] P(strings[t])
+    over t in [offsets[i], offsets[i+1]); strings packed as x | (z << 32)."""
+    dim: int
+    strings: np.ndarray
+    coefs: np.ndarray
+    offsets: np.ndarray
+    status: int
+    report: dict
+
+    def element(self, i: int) -> list[tuple[int, float]]:
+        a, b = int(self.offsets[i]), int(self.offsets[i + 1])
+        return list(zip(self.strings[a:b].tolist(), self.coefs[a:b].tolist()))
+
+
+def lie_closure_pauli(strings, coefs, offsets, n_qubits: int, tol: float, max_dim: int | None = None,
+                      term_capacity: int | None = None, check: bool = True, **opts) -> PauliClosureResult:
+    """Algorithm 4 on sparse Pauli-sum generators (host arrays): generator j is
+    i * sum_t coefs[t] P(strings[t]) over t in [offsets[j], offsets[j+1])."""
+    st_ = np.ascontiguousarray(strings, dtype=np.uint64)
+    cf = np.ascontiguousarray(coefs, dtype=np.float64)
+    of = np.ascontiguousarray(offsets, dtype=np.int64)
+    if st_.shape != cf.shape or of.ndim != 1 or of.size < 2 or int(of[-1]) != st_.size:
+        raise ValueError("strings/coefs must be equal-length 1-d arrays and offsets their k+1 bounds")
+    k = of.size - 1
+    cap = int(max_dim) if max_dim is not None else min(4 ** n_qubits, 1 << 16)
+    tcap = int(term_capacity) if term_capacity is not None else max(min(cap * 4 ** n_qubits, 1 << 22), 1024)
+    out_s = np.zeros(tcap, dtype=np.uint64)
+    out_c = np.zeros(tcap, dtype=np.float64)
+    out_o = np.zeros(cap + 1, dtype=np.int64)
+    dim = ctypes.c_longlong(0)
+    rep = Report()
+    o = make_options("fp64", **opts)
+    stt = lib().lie_closure_pauli(st_.ctypes.data, cf.ctypes.data, of.ctypes.data, k, int(n_qubits), float(tol),
+                                  out_s.ctypes.data, out_c.ctypes.data, out_o.ctypes.data, tcap, ctypes.byref(dim),
+                                  cap, ctypes.byref(o), ctypes.byref(rep))
+    _check(stt, check)
+    n = int(dim.value)
+    nt = int(out_o[n]) if n > 0 else 0
+    return PauliClosureResult(n, out_s[:nt], out_c[:nt], out_o[:n + 1], stt, rep.as_dict())
+
+
+def lie_closure_pauli_dev(strings, coefs, offsets, n_qubits: int, tol: float, max_dim: int,
+                          term_capacity: int, basis_strings=None, basis_coefs=None, basis_offsets=None,
+                          stream=None, check: bool = True, **opts) -> ClosureResult:
+    """As ``lie_closure_pauli`` on torch CUDA tensors (int64 strings, float64
+    coefs, int64 offsets); the optional outputs are device tensors of
+    term_capacity / term_capacity / max_dim + 1 entries."""
+    import torch
+    for t in (strings, coefs, offsets):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("inputs must be contiguous CUDA tensors")
+    k = offsets.numel() - 1
+    s = stream if stream is not None else torch.cuda.current_stream()
+    dim = ctypes.c_longlong(0)
+    rep = Report()
+    o = make_options("fp64", **opts)
+    ptr = lambda t: t.data_ptr() if t is not None else None
+    st = lib().lie_closure_pauli_dev(strings.data_ptr(), coefs.data_ptr(), offsets.data_ptr(), k, int(n_qubits),
+                                     float(tol), ptr(basis_strings), ptr(basis_coefs), ptr(basis_offsets),
+                                     int(term_capacity), ctypes.byref(dim), int(max_dim), ctypes.byref(o),
+                                     ctypes.byref(rep), ctypes.c_void_p(s.cuda_stream))
+    _check(st, check)
+    return ClosureResult(int(dim.value), None, st, rep.as_dict())
+
+
+def pauli_label(string: int, n_qubits: int) -> str:
+    """Letters of a packed string (qubit 1 first)."""
+    x, z = int(string) & 0xFFFFFFFF, int(string) >> 32
+    return "".join("IXZY"[((x >> q) & 1) + 2 * ((z >> q) & 1)] for q in range(n_qubits))
 
 
 def lc_split_gemm_f32(A, B, stream=None):

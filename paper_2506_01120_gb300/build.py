@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblieclosure.so")
-SOURCES = ["lc_api.cu", "lc_fp64.cu", "lc_mixed.cu", "lc_tcgen05.cu", "lc_alg2.cu"]
+SOURCES = ["lc_api.cu", "lc_fp64.cu", "lc_mixed.cu", "lc_tcgen05.cu", "lc_alg2.cu", "lc_pauli.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-fvisibility=hidden"]

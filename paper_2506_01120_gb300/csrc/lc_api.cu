@@ -779,7 +779,7 @@ const char* lc_status_string(int s) {
     case LC_ERR_ARG: return "invalid argument";
     case LC_ERR_NOT_ANTIHERMITIAN: return "generator is not anti-Hermitian";
     case LC_ERR_NONFINITE: return "non-finite value in the generators";
-    case LC_ERR_CAPACITY: return "basis capacity (max_dim) exceeded";
+    case LC_ERR_CAPACITY: return "basis capacity (max_dim, or term_capacity of the Pauli-sum path) exceeded";
     case LC_ERR_CUDA: return "CUDA error";
     case LC_ERR_OOM: return "out of device memory";
     case LC_ERR_TIMEOUT: return "device wait timed out";

@@ -56,6 +56,66 @@ def generators_from_labels(labels) -> np.ndarray:
     return np.stack([1j * pauli_matrix(s) for s in labels]).astype(np.complex128)
 
 
+def pauli_string(label: str) -> int:
+    """Packed string x | (z << 32) of a Pauli label: bit q of x (z) is set when
+    qubit q+1 carries X or Y (Z or Y)."""
+    x = z = 0
+    for q, ch in enumerate(label):
+        if ch in "XY":
+            x |= 1 << q
+        if ch in "ZY":
+            z |= 1 << q
+    return x | (z << 32)
+
+
+def pauli_sum_terms(ops):
+    """Sparse generator arrays for the Pauli-sum entry point.  ``ops`` is a list
+    of operators, each a list of (label, coefficient) pairs standing for
+    i * sum coefficient * P(label).  Returns (strings uint64, coefs float64,
+    offsets int64)."""
+    strings, coefs, offsets = [], [], [0]
+    for op in ops:
+        for label, c in op:
+            strings.append(pauli_string(label))
+            coefs.append(float(c))
+        offsets.append(len(strings))
+    return (np.array(strings, dtype=np.uint64), np.array(coefs, dtype=np.float64),
+            np.array(offsets, dtype=np.int64))
+
+
+def pauli_sum_matrix(op, n: int) -> np.ndarray:
+    """Dense i * sum c P(label) of one Pauli-sum operator."""
+    out = np.zeros((2 ** n, 2 ** n), dtype=np.complex128)
+    for label, c in op:
+        out += 1j * c * pauli_matrix(label)
+    return out
+
+
+def tfim_ops(n: int) -> list:
+    """Transverse-field Ising generators on an open chain: sum_j X_j and
+    sum_j Z_j Z_{j+1}, unit coefficients."""
+    xs = [("I" * j + "X" + "I" * (n - j - 1), 1.0) for j in range(n)]
+    zz = [("I" * j + "ZZ" + "I" * (n - j - 2), 1.0) for j in range(n - 1)]
+    return [xs, zz]
+
+
+def random_pauli_sums(n: int, k: int, terms: int, seed: int) -> list:
+    """k operators of ``terms`` random non-identity strings each (letters
+    uniform over I, X, Y, Z per qubit, redrawn if all I) with N(0, 1)
+    coefficients, from default_rng(seed)."""
+    rng = np.random.default_rng(seed)
+    ops = []
+    for _ in range(k):
+        op = []
+        while len(op) < terms:
+            label = "".join("IXYZ"[int(v)] for v in rng.integers(0, 4, size=n))
+            if set(label) == {"I"}:
+                continue
+            op.append((label, float(rng.standard_normal())))
+        ops.append(op)
+    return ops
+
+
 def so2n_chain_labels(n: int) -> list[str]:
     """{X_j} and {Z_jZ_{j+1}} on an open chain of n qubits."""
     return chain_labels(n, singles=("X",), zz=True)

@@ -96,3 +96,30 @@ def test_argument_errors_need_no_gpu(built_lib):
     o.precision = 7
     assert L.lie_closure(g.ctypes.data, 1, 4, 1e-8, None, ctypes.byref(dim), 16, ctypes.byref(o), None) \
         == binding.LC_ERR_ARG
+
+
+def test_pauli_entry_rejects_bad_arguments_before_any_device_call(built_lib):
+    """Argument errors of lie_closure_pauli are found on the host (no GPU needed)."""
+    import numpy as np
+    L = built_lib
+    s = np.array([1, 2], dtype=np.uint64)
+    c = np.array([1.0, 1.0])
+    good = np.array([0, 1, 2], dtype=np.int64)
+    out_s = np.zeros(8, dtype=np.uint64)
+    out_c = np.zeros(8)
+    out_o = np.zeros(9, dtype=np.int64)
+    dim = ctypes.c_longlong(7)
+
+    def call(off, nq=2, tol=1e-8, k=2, tcap=8, max_dim=8):
+        return L.lie_closure_pauli(s.ctypes.data, c.ctypes.data, off.ctypes.data, k, nq, tol, out_s.ctypes.data,
+                                   out_c.ctypes.data, out_o.ctypes.data, tcap, ctypes.byref(dim), max_dim, None, None)
+
+    assert call(good, nq=0) == binding.LC_ERR_ARG
+    assert call(good, nq=32) == binding.LC_ERR_ARG
+    assert call(good, tol=0.0) == binding.LC_ERR_ARG
+    assert call(good, k=0) == binding.LC_ERR_ARG
+    assert call(good, tcap=0) == binding.LC_ERR_ARG
+    assert call(good, max_dim=0) == binding.LC_ERR_ARG
+    assert call(np.array([1, 1, 2], dtype=np.int64)) == binding.LC_ERR_ARG      # offsets[0] != 0
+    assert call(np.array([0, 2, 1], dtype=np.int64)) == binding.LC_ERR_ARG      # decreasing
+    assert dim.value == 0

@@ -319,3 +319,21 @@ def test_alg2_same_algebra(case):
         assert oc.norm(b) == pytest.approx(1.0, abs=1e-13)
     G = oc.gram(r2.B)
     assert np.max(np.abs(G @ r2.A_inv - np.eye(r2.dim))) < 1e-8
+
+
+def test_packed_pauli_strings_follow_the_oracle_bit_convention():
+    """The Pauli-sum entry point's packed strings (x | z << 32) carry the same
+    (x, z) bits as the oracle's symplectic encoding, and a product string is the
+    XOR of the two (up to phase), checked on matrices."""
+    import itertools
+    from paper_2506_01120_gb300 import inputs
+    for label in ["X", "Y", "Z", "XYZ", "IZY", "YYIX"]:
+        x, z = oc.pauli_to_bits(label)
+        assert inputs.pauli_string(label) == x | (z << 32)
+    for a, b in itertools.product(["XY", "ZI", "YZ", "XX"], repeat=2):
+        pa, pb = inputs.pauli_string(a), inputs.pauli_string(b)
+        prod = inputs.pauli_matrix(a) @ inputs.pauli_matrix(b)
+        x, z = (pa ^ pb) & 0xFFFFFFFF, (pa ^ pb) >> 32
+        ref = inputs.pauli_matrix(oc.bits_to_pauli(x, z, 2))
+        ratio = prod[np.nonzero(ref)] / ref[np.nonzero(ref)]
+        assert np.allclose(ratio, ratio[0]) and abs(abs(ratio[0]) - 1) < 1e-15
