@@ -11,7 +11,9 @@ time-to-closure, the roofline of the dominant kernel (the split-BF16 tcgen05
 screening GEMM, event-timed inside the library on the call's stream), the
 end-to-end number through the host API (host->device copy of the generators,
 device->host copy of the basis), the FP64 GPU path on a bounded prefix of the
-same sweep, and the CPU oracle on a bounded sample.
+same sweep, the sparse Pauli-sum form of the method on the same generators at
+6 and 7 qubits (the workloads of the paper's Table 2), and the CPU oracle on a
+bounded sample.
 
 ``--impl reference`` times the CPU oracle instead (the paper has no code; the
 oracle is the reference arm) on bounded samples of the same workload.
@@ -51,6 +53,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-seconds", type=float, default=0.0,
                     help="reference arm: oracle seconds per step (0 = about a minute in total)")
+    ap.add_argument("--pauli-steps", type=int, default=3,
+                    help="timed closures per sparse Pauli-sum workload (0 = skip)")
+    ap.add_argument("--pauli-qubits", type=int, nargs="*", default=[6, 7],
+                    help="qubit counts of the sparse hardware-efficient-ansatz workloads")
+    ap.add_argument("--pauli-only", action="store_true", help="run only the sparse Pauli-sum leg")
     return ap.parse_args()
 
 
@@ -204,6 +211,81 @@ def run_reference(args, world, rank, pg):
 
 
 # ------------------------------------------------------------ GPU legs
+# Table 2 of the paper (many-core CPU, sparse Pauli sums): seconds per closure
+PAPER_TABLE2_S = {6: 429.0, 7: 2345.0}
+# algorithmic bytes the screen moves per candidate when every basis element is
+# one string: offsets of both operands (32 B), their string and coefficient
+# (32 B), the index probe (12 B) and chain entry (16 B), the projected
+# element's offsets and term (32 B), the flag (1 B)
+PAULI_SCREEN_BYTES_PER_CAND = 125
+
+
+def pauli_leg(args, stream, peaks, peak_src):
+    """Sparse Pauli-sum closures of the hardware-efficient-ansatz generators
+    (iX_j, iY_j, iZ_jZ_{j+1}) through lie_closure_pauli_dev (resident inputs)
+    and lie_closure_pauli (host arrays in, basis out)."""
+    import numpy as np
+    import torch
+
+    from paper_2506_01120_gb300 import binding, inputs
+    out = []
+    for n in args.pauli_qubits:
+        labels = inputs.su2n_chain_labels(n)
+        s, c, o = inputs.pauli_sum_terms([[(l, 1.0)] for l in labels])
+        D = 4 ** n - 1
+        cap, tcap = D + 1, 2 * (D + 1)
+        ds, dc, do = (torch.from_numpy(s.view(np.int64)).cuda(), torch.from_numpy(c).cuda(),
+                      torch.from_numpy(o).cuda())
+        bs = torch.empty(tcap, dtype=torch.int64, device="cuda")
+        bc = torch.empty(tcap, dtype=torch.float64, device="cuda")
+        bo = torch.empty(cap + 1, dtype=torch.int64, device="cuda")
+
+        def run():
+            return binding.lie_closure_pauli_dev(ds, dc, do, n, 1e-8, cap, tcap, bs, bc, bo, stream=stream,
+                                                 profile=1)
+        run()
+        torch.cuda.synchronize()
+        times, reps = [], []
+        for _ in range(args.pauli_steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = run()
+            b.record(stream)
+            torch.cuda.synchronize()
+            assert r.dim == D, (n, r.dim)
+            times.append(a.elapsed_time(b) * 1e-3)
+            reps.append(r.report)
+        cand = reps[0]["brackets_checked"] + reps[0]["generators_checked"]
+        t = sum(times) / len(times)
+        t_screen = sum(rp["t_phase_s"][3] for rp in reps) / len(reps)
+        t_accept = sum(rp["t_phase_s"][4] for rp in reps) / len(reps)
+        screened = reps[0]["brackets_checked"]
+        gbs = PAULI_SCREEN_BYTES_PER_CAND * screened / t_screen / 1e9 if t_screen > 0 else 0.0
+        hw = []
+        for _ in range(2):
+            t0 = time.perf_counter()
+            rh = binding.lie_closure_pauli(s, c, o, n, 1e-8, max_dim=cap, term_capacity=tcap)
+            hw.append(time.perf_counter() - t0)
+            assert rh.dim == D
+        te = min(hw)
+        out.append({
+            "workload": f"hea_n{n}_pauli", "qubits": n, "closure_dim": D, "candidates": cand,
+            "value": cand / t, "unit": UNIT, "time_to_closure_s": t, "t_last_accept_s": reps[-1]["t_last_accept_s"],
+            "phase_s": {"screen": t_screen, "accept": t_accept, "other": max(0.0, t - t_screen - t_accept)},
+            "screen_launches": reps[0]["gemm_launches"], "gpu_launches": reps[0]["kernel_launches"],
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                         "frac": gbs / float(peaks["hbm_gbs"]), "traffic": None, "kernel": "k_pauli_screen",
+                         "bytes_per_candidate": PAULI_SCREEN_BYTES_PER_CAND,
+                         "peak_source": f"hbm_gbs ({peak_src})",
+                         "note": "working set (basis, index) is L2-resident; latency-bound"},
+            "e2e": {"value": cand / te, "unit": UNIT, "time_to_closure_s": te,
+                    "h2d_bytes_per_step": int(s.nbytes + c.nbytes + o.nbytes),
+                    "d2h_bytes_per_step": int(D * 16 + (D + 1) * 8)},
+            "paper_table2_cpu_s": PAPER_TABLE2_S.get(n),
+        })
+    return out
+
+
 def run_ours(args, world, rank, local, pg):
     import numpy as np
     import torch
@@ -215,6 +297,12 @@ def run_ours(args, world, rank, local, pg):
     if rank == 0 and not os.path.exists(binding.LIB_PATH):
         build()
     barrier(pg)
+    if args.pauli_only:
+        peaks, peak_src = measured_peaks()
+        sp = pauli_leg(args, torch.cuda.current_stream(), peaks, peak_src)
+        if rank == 0:
+            print(json.dumps({"sparse_pauli": sp}), flush=True)
+        return
     g, _ = inputs.workload_generators(WORKLOAD)
     k, d = g.shape[0], g.shape[1]
     tol = 1e-8
@@ -303,6 +391,8 @@ def run_ours(args, world, rank, local, pg):
                 "mixed_brackets_per_s_same_prefix": nf / rm.report["t_total_s"],
                 "fp64_time_s": rf.report["t_total_s"], "mixed_time_s": rm.report["t_total_s"]}
 
+    sparse = pauli_leg(args, stream, peaks, peak_src) if args.pauli_steps > 0 else None
+
     cpu = None
     if rank == 0 and args.cpu_seconds > 0:
         rate, c, w, cores = oracle_sample(args.cpu_seconds)
@@ -332,6 +422,7 @@ def run_ours(args, world, rank, local, pg):
                      "peak_source": f"bf16_tflops_sustained ({peak_src})"},
         "e2e": e2e,
         "fp64_gpu": fp64,
+        "sparse_pauli": sparse,
         "cpu_baseline": cpu,
         "gpu_launches": int(sum(rep["kernel_launches"] for rep in reports)),
         "clocks": clocks,

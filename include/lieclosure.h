@@ -299,8 +299,15 @@ LC_API int lie_closure_batched(int nsets, const lc_c128* const* generators, cons
  *              block (0 = 2^20), opt->fault_inject = 2 starts the per-candidate
  *              hash tables at their smallest size (a test hook that exercises
  *              the regrow path).
+ * Report: brackets_checked, n_flagged, cursor and the residual margins as in
+ * lie_closure; gemm_launches counts screen launches here, and with
+ * opt->profile t_phase_s[3] / t_phase_s[4] are the device times of the screen
+ * and of the in-order accept.
+ * Limits: a candidate's terms (and its residual's) must fit 4096 distinct
+ * strings and its projection 2048 basis elements (the per-warp tables in
+ * shared memory, filled at most half); dense operators belong to lie_closure.
  * Returns LC_OK, LC_ERR_ARG, LC_ERR_NONFINITE, LC_ERR_CAPACITY (basis,
- * term or per-candidate hash capacity exceeded; *dim_out elements are valid),
+ * term or per-candidate table capacity exceeded; *dim_out elements are valid),
  * LC_ERR_CUDA or LC_ERR_OOM.
  */
 LC_API int lie_closure_pauli(const unsigned long long* strings, const double* coefs,

@@ -171,6 +171,17 @@ struct PState {
   int nflag, nnonzero, noverflow;   // screen counters of the current block
 };
 
+// pair index t = l(l-1)/2 + m -> (l, m): a single-precision square root
+// estimate (relative error below 2^-22, so off by one at most while l < 2^21)
+// made exact by integer steps; FP64 throughput is low on this part.
+__device__ __forceinline__ void pair_of(long long t, int* l, int* m) {
+  long long L = (long long)((1.0f + sqrtf(1.0f + 8.0f * (float)t)) * 0.5f);
+  while (L > 1 && L * (L - 1) / 2 > t) --L;
+  while ((L + 1) * L / 2 <= t) ++L;
+  *l = (int)L;
+  *m = (int)(t - L * (L - 1) / 2);
+}
+
 template <bool RO>
 __device__ __forceinline__ int index_head(const PBasis& B, u64 s) {
   uint32_t i = slot_hash(s) & B.imask;
@@ -207,7 +218,7 @@ __device__ bool form(const PBasis& B, const PSrc& G, bool gen, long long id, con
     for (long long q = a0 + lane; q < a1; q += 32) ok &= table_add(h, G.key[q], G.val[q]);
   } else {
     int l, m;
-    pair_from_index(id, &l, &m);
+    pair_of(id, &l, &m);
     const long long a0 = ld<RO>(&B.off[l]), b0 = ld<RO>(&B.off[m]);
     const long long ta = ld<RO>(&B.off[l + 1]) - a0, tb = ld<RO>(&B.off[m + 1]) - b0;
     const long long tot = ta * tb;
@@ -494,6 +505,8 @@ class ClosureP {
     K_ = o.block_k > 0 ? o.block_k : (1 << 20);
   }
   ~ClosureP() {
+    for (cudaEvent_t& e : ev_)
+      if (e) cudaEventDestroy(e);
     if (base_) cudaFreeAsync(base_, s_);
     if (hs_) cudaFreeHost(hs_);
   }
@@ -549,6 +562,9 @@ class ClosureP {
       }
       rep->tau_screen = 0.5 * tol_;
       rep->kernel_launches = launches_;
+      rep->gemm_launches = screens_;       // here: screen launches
+      rep->t_phase_s[3] = t_screen_;
+      rep->t_phase_s[4] = t_accept_;
       rep->precision = LC_PREC_FP64;
       rep->status = rc;
     }
@@ -572,7 +588,21 @@ class ClosureP {
   int hsl_ = 64, bsl_ = 32, hacc_ = 256, bacc_ = 128, maxT_ = 0, maxTg_ = 0;
   bool trace_ = false;
   long long N_ = 0, T_ = 0, t_ = 0, checked_ = 0, flagged_ = 0, nonzero_ = 0, blocks_ = 0, launches_ = 0;
-  double t_start_ = 0.0, t_last_ = 0.0;
+  double t_start_ = 0.0, t_last_ = 0.0, t_screen_ = 0.0, t_accept_ = 0.0;
+  long long screens_ = 0;
+  cudaEvent_t ev_[4] = {nullptr, nullptr, nullptr, nullptr};   // with opt.profile: screen, accept
+
+  bool profiling() {
+    if (!opt_.profile) return false;
+    if (!ev_[0])
+      for (cudaEvent_t& e : ev_)
+        if (cudaEventCreate(&e) != cudaSuccess) return false;
+    return true;
+  }
+  static double elapsed(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    return cudaEventElapsedTime(&ms, a, b) == cudaSuccess ? 1e-3 * ms : 0.0;
+  }
   int nsm_ = 152;
 
   static double bits_to_double(unsigned long long b) {
@@ -659,12 +689,16 @@ class ClosureP {
       LP_TRY(cudaMemcpyAsync(&ps_->start, &hs_->start, sizeof(int), cudaMemcpyHostToDevice, s_));
       const size_t sm = 16ull * (hacc_ + bacc_);
       LP_TRY(cudaFuncSetAttribute(k_pauli_accept, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      const bool prof = profiling();
+      if (prof) cudaEventRecord(ev_[2], s_);
       k_pauli_accept<<<1, 32, sm, s_>>>(B_, G_, gen ? 1 : 0, t0, count, flag_, chunks_, hacc_, bacc_, tol_, eta_,
                                         (int)ncap_, tcap_, ps_);
+      if (prof) cudaEventRecord(ev_[3], s_);
       ++launches_;
       LP_TRY(cudaGetLastError());
       int rc = read_state();
       if (rc != LC_OK) return rc;
+      if (prof) t_accept_ += elapsed(ev_[2], ev_[3]);
       const long long before = N_;
       N_ = hs_->n;
       T_ = hs_->tused;
@@ -718,12 +752,17 @@ class ClosureP {
       LP_TRY(cudaFuncSetAttribute(k_pauli_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
       const long long want = (count + warps - 1) / warps;
       const int grid = (int)std::max<long long>(1, std::min<long long>(want, 8ll * nsm_));
+      const bool prof = profiling();
+      if (prof) cudaEventRecord(ev_[0], s_);
       k_pauli_screen<<<grid, 32 * warps, sm, s_>>>(B_, t_, count, (int)N_, hsl_, bsl_, tol_, eta_, flag_, chunks_,
                                                    ps_);
+      if (prof) cudaEventRecord(ev_[1], s_);
+      ++screens_;
       ++launches_;
       LP_TRY(cudaGetLastError());
       const long long n_before = N_;
       int rc = accept(false, t_, count);
+      if (prof) t_screen_ += elapsed(ev_[0], ev_[1]);
       nonzero_ += hs_->nnonzero;
       flagged_ += hs_->nflag + hs_->noverflow;
       ++blocks_;
