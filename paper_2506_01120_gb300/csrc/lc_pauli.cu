@@ -169,6 +169,8 @@ struct PState {
   int naccepted;     // accepts so far
   unsigned long long min_acc_bits, max_rej_bits, max_screen_rej_bits;
   int nflag, nnonzero, noverflow;   // screen counters of the current block
+  int npure;         // flagged candidates that are one string absent from the basis
+  int nfirst;        // distinct strings among them (first occurrences in pair order)
 };
 
 // pair index t = l(l-1)/2 + m -> (l, m): a single-precision square root
@@ -282,14 +284,15 @@ __device__ __forceinline__ Table warp_table(unsigned char* base, int slots, int*
 __global__ void __launch_bounds__(256) k_pauli_screen(PBasis B, long long t0, int count, int nrows, int hslots,
                                                       int bslots, double tol, double eta,
                                                       unsigned char* __restrict__ flag,
-                                                      unsigned* __restrict__ chunks, PState* ps) {
+                                                      unsigned* __restrict__ chunks, u64* __restrict__ pkey,
+                                                      double* __restrict__ pval, PState* ps) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int used[2 * 8];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, warps = blockDim.x >> 5;
   unsigned char* base = smem + (size_t)w * 16 * (hslots + bslots);
   const Table h = warp_table(base, hslots, &used[2 * w]), bt = warp_table(base + 16ull * hslots, bslots, &used[2 * w + 1]);
   const PSrc none{nullptr, nullptr, nullptr};
-  int nz = 0, nf = 0, nov = 0;
+  int nz = 0, nf = 0, nov = 0, npure = 0;
   double maxrej = 0.0;
   const double eta2 = eta * eta, tau2 = 0.25 * tol * tol;
   for (long long c = (long long)blockIdx.x * warps + w; c < count; c += (long long)gridDim.x * warps) {
@@ -311,6 +314,25 @@ __global__ void __launch_bounds__(256) k_pauli_screen(PBasis B, long long t0, in
           if (r2 > tau2 * h2) {
             fl = 1;
             ++nf;
+            // pure: no basis element shares a string with h (beta empty, so
+            // the residual is h) and h has one non-zero term
+            if (*const_cast<volatile int*>(bt.used) == 0) {
+              int nnz = 0;
+              for (uint32_t q0 = 0; q0 <= h.mask; q0 += 32) {
+                const uint32_t q = q0 + lane;
+                const bool on = h.key[q] != kEmpty && h.val[q] != 0.0;
+                const unsigned bal = __ballot_sync(kFull, on);
+                if (on && nnz + __popc(bal & ((1u << lane) - 1u)) == 0) {
+                  pkey[c] = h.key[q];
+                  pval[c] = h.val[q];
+                }
+                nnz += __popc(bal);
+              }
+              if (nnz == 1) {
+                fl = 2;
+                ++npure;
+              }
+            }
           } else {
             maxrej = fmax(maxrej, sqrt(r2 / h2));
           }
@@ -327,7 +349,136 @@ __global__ void __launch_bounds__(256) k_pauli_screen(PBasis B, long long t0, in
     if (nz) atomicAdd(&ps->nnonzero, nz);
     if (nf) atomicAdd(&ps->nflag, nf);
     if (nov) atomicAdd(&ps->noverflow, nov);
+    if (npure) atomicAdd(&ps->npure, npure);
     if (maxrej > 0.0) atomicMax(&ps->max_screen_rej_bits, (unsigned long long)__double_as_longlong(maxrej));
+  }
+}
+
+// ------------------------------------------------ blocks of pure candidates
+// When every flagged candidate of a block is pure (one string, absent from the
+// block-start basis), the in-order test reduces to string equality: a pure
+// candidate is dependent on the basis plus the earlier accepts exactly when an
+// earlier candidate of the block carries the same string.  So the accepts are
+// the first occurrence of each string, appended in pair order, each
+// normalised like the sequential step (v / sqrt(v * v)).
+
+// first occurrence of each pure string: dmin[slot of s] = min position
+__global__ void k_pure_first(const unsigned char* __restrict__ flag, const u64* __restrict__ pkey, int count,
+                             u64* __restrict__ dkey, int* __restrict__ dmin, uint32_t dmask) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < count;
+       c += (long long)gridDim.x * blockDim.x) {
+    if (flag[c] != 2) continue;
+    const u64 s = pkey[c];
+    uint32_t i = slot_hash(s) & dmask;
+    for (uint32_t p = 0; p <= dmask; ++p) {
+      const u64 cur = atomicCAS(&dkey[i], kEmpty, s);
+      if (cur == kEmpty || cur == s) {
+        atomicMin(&dmin[i], (int)c);
+        break;
+      }
+      i = (i + 1) & dmask;
+    }
+  }
+}
+
+// per 1024-position chunk: how many first occurrences (one warp per chunk)
+__global__ void k_pure_count(const unsigned char* __restrict__ flag, const u64* __restrict__ pkey, int count,
+                             const u64* __restrict__ dkey, const int* __restrict__ dmin, uint32_t dmask,
+                             unsigned char* __restrict__ first, int* __restrict__ ccount, int nchunks) {
+  const int ch = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (ch >= nchunks) return;
+  int n = 0;
+  for (int b = ch << 10; b < min(count, (ch + 1) << 10); b += 32) {
+    const int c = b + lane;
+    bool f = false;
+    if (c < count && flag[c] == 2) {
+      const u64 s = pkey[c];
+      uint32_t i = slot_hash(s) & dmask;
+      for (uint32_t p = 0; p <= dmask; ++p) {
+        const u64 cur = dkey[i];
+        if (cur == s) {
+          f = dmin[i] == c;
+          break;
+        }
+        if (cur == kEmpty) break;
+        i = (i + 1) & dmask;
+      }
+    }
+    if (c < count) first[c] = f ? 1 : 0;
+    n += __popc(__ballot_sync(kFull, f));
+  }
+  if (lane == 0) ccount[ch] = n;
+}
+
+// exclusive scan of the chunk counts (one block of 1024 threads, nchunks <= 1024 * 64)
+__global__ void __launch_bounds__(1024) k_pure_scan(int* __restrict__ ccount, int nchunks, PState* ps) {
+  __shared__ int part[1024];
+  const int per = (nchunks + 1023) / 1024;
+  const int a = threadIdx.x * per, b = min(nchunks, a + per);
+  int sum = 0;
+  for (int i = a; i < b; ++i) sum += ccount[i];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {   // Hillis-Steele inclusive scan
+    const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = part[threadIdx.x] - sum;
+  for (int i = a; i < b; ++i) {
+    const int v = ccount[i];
+    ccount[i] = run;
+    run += v;
+  }
+  if (threadIdx.x == 1023) ps->nfirst = part[1023];
+}
+
+__device__ __forceinline__ int pure_take(const PState* ps, int n0, long long t0terms, int ncap, long long tcap) {
+  return (int)min((long long)ps->nfirst, min((long long)(ncap - n0), tcap - t0terms));
+}
+
+// append the first occurrences in pair order (one warp per chunk), as many as
+// fit the free rows and terms
+__global__ void k_pure_append(PBasis B, const unsigned char* __restrict__ first, const u64* __restrict__ pkey,
+                              const double* __restrict__ pval, int count, const int* __restrict__ coff,
+                              int nchunks, int n0, long long t0terms, int ncap, long long tcap,
+                              const PState* ps) {
+  const int ch = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (ch >= nchunks) return;
+  const int take = pure_take(ps, n0, t0terms, ncap, tcap);
+  int rank = coff[ch];
+  for (int b = ch << 10; b < min(count, (ch + 1) << 10); b += 32) {
+    const int c = b + lane;
+    const bool f = c < count && first[c];
+    const unsigned bal = __ballot_sync(kFull, f);
+    if (f) {
+      const int i = rank + __popc(bal & ((1u << lane) - 1u));
+      if (i < take) {
+        const double v = pval[c];
+        const double r2 = fma(v, v, 0.0);
+        const long long pos = t0terms + i;
+        const u64 s = pkey[c];
+        B.key[pos] = s;
+        B.val[pos] = v * (1.0 / sqrt(r2));
+        B.row[pos] = n0 + i;
+        B.off[n0 + i + 1] = pos + 1;
+        index_push(B, s, (int)pos);
+      }
+    }
+    rank += __popc(bal);
+  }
+}
+
+__global__ void k_pure_commit(PState* ps, int n0, long long t0terms, int ncap, long long tcap) {
+  const int take = pure_take(ps, n0, t0terms, ncap, tcap);
+  ps->n = n0 + take;
+  ps->tused = t0terms + take;
+  ps->naccepted += take;
+  ps->why = take < ps->nfirst ? 2 : 0;
+  if (take > 0) {
+    ps->maxT = max(ps->maxT, 1);
+    atomicMin(&ps->min_acc_bits, (unsigned long long)__double_as_longlong(1.0));
   }
 }
 
@@ -583,6 +734,14 @@ class ClosureP {
   PBasis B_{};
   PSrc G_{};
   unsigned char* flag_ = nullptr;
+  u64* pkey_ = nullptr;          // pure candidates: string and coefficient
+  double* pval_ = nullptr;
+  unsigned char* first_ = nullptr;
+  int* ccount_ = nullptr;        // per-chunk counts, then offsets
+  u64* dkey_ = nullptr;          // first-occurrence table
+  int* dmin_ = nullptr;
+  long long dslots_ = 64;
+  long long pure_blocks_ = 0;
   unsigned* chunks_ = nullptr;
   int* bad_ = nullptr;
   int hsl_ = 64, bsl_ = 32, hacc_ = 256, bacc_ = 128, maxT_ = 0, maxTg_ = 0;
@@ -621,6 +780,10 @@ class ClosureP {
     const size_t oO = take(8ull * (ncap_ + 1)), oIK = take(8ull * islots), oIH = take(4ull * islots);
     const size_t oF = take(Kc), oC = take(4ull * ((Kc + 32767) / 32768 + 1)), oS = take(sizeof(PState)),
                  oB = take(16);
+    dslots_ = 64;
+    while (dslots_ < 2 * (long long)Kc) dslots_ <<= 1;
+    const size_t oPK = take(8ull * Kc), oPV = take(8ull * Kc), oFi = take(Kc), oCC = take(4ull * ((Kc + 1023) / 1024)),
+                 oDK = take(8ull * dslots_), oDM = take(4ull * dslots_);
     int dev = 0;
     LP_TRY(cudaGetDevice(&dev));
     LP_TRY(cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, dev));
@@ -637,6 +800,12 @@ class ClosureP {
     B_.imask = (uint32_t)(islots - 1);
     flag_ = (unsigned char*)at(oF);
     chunks_ = (unsigned*)at(oC);
+    pkey_ = (u64*)at(oPK);
+    pval_ = (double*)at(oPV);
+    first_ = (unsigned char*)at(oFi);
+    ccount_ = (int*)at(oCC);
+    dkey_ = (u64*)at(oDK);
+    dmin_ = (int*)at(oDM);
     ps_ = (PState*)at(oS);
     bad_ = (int*)at(oB);
     LP_TRY(cudaMemsetAsync(B_.off, 0, sizeof(long long) * (ncap_ + 1), s_));
@@ -715,6 +884,40 @@ class ClosureP {
     }
   }
 
+  // a block whose flagged candidates are all pure: first occurrences in
+  // pair order, appended in parallel
+  int pure_block(int count) {
+    long long ds = 64;
+    while (ds < 2ll * hs_->npure) ds <<= 1;
+    const uint32_t dmask = (uint32_t)(ds - 1);
+    const int nchunks = (count + 1023) / 1024;
+    const bool prof = profiling();
+    if (prof) cudaEventRecord(ev_[2], s_);
+    LP_TRY(cudaMemsetAsync(dkey_, 0xff, 8ull * ds, s_));
+    LP_TRY(cudaMemsetAsync(dmin_, 0x7f, 4ull * ds, s_));
+    const int g1 = (int)std::min<long long>((count + 255) / 256, 8ll * nsm_);
+    k_pure_first<<<g1, 256, 0, s_>>>(flag_, pkey_, count, dkey_, dmin_, dmask);
+    const int g2 = (nchunks + 7) / 8;
+    k_pure_count<<<g2, 256, 0, s_>>>(flag_, pkey_, count, dkey_, dmin_, dmask, first_, ccount_, nchunks);
+    k_pure_scan<<<1, 1024, 0, s_>>>(ccount_, nchunks, ps_);
+    k_pure_append<<<g2, 256, 0, s_>>>(B_, first_, pkey_, pval_, count, ccount_, nchunks, (int)N_, T_, (int)ncap_,
+                                       tcap_, ps_);
+    k_pure_commit<<<1, 1, 0, s_>>>(ps_, (int)N_, T_, (int)ncap_, tcap_);
+    if (prof) cudaEventRecord(ev_[3], s_);
+    launches_ += 5;
+    ++pure_blocks_;
+    LP_TRY(cudaGetLastError());
+    const int rc = read_state();
+    if (rc != LC_OK) return rc;
+    if (prof) t_accept_ += elapsed(ev_[2], ev_[3]);
+    const long long before = N_;
+    N_ = hs_->n;
+    T_ = hs_->tused;
+    maxT_ = hs_->maxT;
+    if (N_ > before) t_last_ = now_s();
+    return hs_->why == 2 ? LC_ERR_CAPACITY : LC_OK;
+  }
+
   int generator_pass() {
     const int rc = accept(true, 0, k_);
     if (opt_.verbose) fprintf(stderr, "lieclosure-pauli: generators %d -> dim %lld\n", k_, N_);
@@ -744,8 +947,8 @@ class ClosureP {
       if (kb <= 0) break;
       const int count = (int)kb;
       // per-block counters and chunk bits
-      hs_->nflag = hs_->nnonzero = hs_->noverflow = 0;
-      LP_TRY(cudaMemcpyAsync(&ps_->nflag, &hs_->nflag, 3 * sizeof(int), cudaMemcpyHostToDevice, s_));
+      hs_->nflag = hs_->nnonzero = hs_->noverflow = hs_->npure = hs_->nfirst = 0;
+      LP_TRY(cudaMemcpyAsync(&ps_->nflag, &hs_->nflag, 5 * sizeof(int), cudaMemcpyHostToDevice, s_));
       LP_TRY(cudaMemsetAsync(chunks_, 0, 4ull * ((count + 32767) / 32768 + 1), s_));
       const int warps = std::max(1, std::min(8, (96 * 1024) / (16 * (hsl_ + bsl_))));
       const size_t sm = 16ull * (hsl_ + bsl_) * warps;
@@ -755,22 +958,30 @@ class ClosureP {
       const bool prof = profiling();
       if (prof) cudaEventRecord(ev_[0], s_);
       k_pauli_screen<<<grid, 32 * warps, sm, s_>>>(B_, t_, count, (int)N_, hsl_, bsl_, tol_, eta_, flag_, chunks_,
-                                                   ps_);
+                                                   pkey_, pval_, ps_);
       if (prof) cudaEventRecord(ev_[1], s_);
       ++screens_;
       ++launches_;
       LP_TRY(cudaGetLastError());
       const long long n_before = N_;
-      int rc = accept(false, t_, count);
+      int rc = read_state();
+      if (rc != LC_OK) return rc;
       if (prof) t_screen_ += elapsed(ev_[0], ev_[1]);
+      if (hs_->nflag + hs_->noverflow == 0) {
+        rc = LC_OK;                                  // nothing to decide
+      } else if (hs_->noverflow == 0 && hs_->npure == hs_->nflag) {
+        rc = pure_block(count);
+      } else {
+        rc = accept(false, t_, count);
+      }
       nonzero_ += hs_->nnonzero;
       flagged_ += hs_->nflag + hs_->noverflow;
       ++blocks_;
       t_ += kb;
       checked_ += kb;
       if (opt_.verbose)
-        fprintf(stderr, "lieclosure-pauli: block %lld t=%lld kb=%lld flagged=%d overflow=%d dim %lld -> %lld\n",
-                blocks_, t_ - kb, kb, hs_->nflag, hs_->noverflow, n_before, N_);
+        fprintf(stderr, "lieclosure-pauli: block %lld t=%lld kb=%lld flagged=%d (pure %d) overflow=%d dim %lld -> %lld\n",
+                blocks_, t_ - kb, kb, hs_->nflag, hs_->npure, hs_->noverflow, n_before, N_);
       if (rc != LC_OK) return rc;
       if (hs_->noverflow > count / 64) {   // screen tables too small for this basis
         hsl_ = std::min(hsl_ * 2, kScreenMaxSlots);
