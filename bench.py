@@ -213,11 +213,11 @@ def run_reference(args, world, rank, pg):
 # ------------------------------------------------------------ GPU legs
 # Table 2 of the paper (many-core CPU, sparse Pauli sums): seconds per closure
 PAPER_TABLE2_S = {6: 429.0, 7: 2345.0}
-# algorithmic bytes the screen moves per candidate when every basis element is
-# one string: offsets of both operands (32 B), their string and coefficient
-# (32 B), the index probe (12 B) and chain entry (16 B), the projected
-# element's offsets and term (32 B), the flag (1 B)
-PAULI_SCREEN_BYTES_PER_CAND = 125
+# algorithmic bytes of the one-string screen (k_pauli_screen1) per candidate:
+# the two operand strings (16 B) and the flag (1 B), plus for anticommuting
+# pairs the index probe (string 8 B + head 4 B)
+def pauli_screen_bytes(candidates: int, anticommuting: int) -> float:
+    return 17.0 * candidates + 12.0 * anticommuting
 
 
 def pauli_leg(args, stream, peaks, peak_src):
@@ -260,7 +260,8 @@ def pauli_leg(args, stream, peaks, peak_src):
         t_screen = sum(rp["t_phase_s"][3] for rp in reps) / len(reps)
         t_accept = sum(rp["t_phase_s"][4] for rp in reps) / len(reps)
         screened = reps[0]["brackets_checked"]
-        gbs = PAULI_SCREEN_BYTES_PER_CAND * screened / t_screen / 1e9 if t_screen > 0 else 0.0
+        nbytes = pauli_screen_bytes(screened, reps[0]["n_nonzero"])
+        gbs = nbytes / t_screen / 1e9 if t_screen > 0 else 0.0
         hw = []
         for _ in range(2):
             t0 = time.perf_counter()
@@ -274,10 +275,10 @@ def pauli_leg(args, stream, peaks, peak_src):
             "phase_s": {"screen": t_screen, "accept": t_accept, "other": max(0.0, t - t_screen - t_accept)},
             "screen_launches": reps[0]["gemm_launches"], "gpu_launches": reps[0]["kernel_launches"],
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                         "frac": gbs / float(peaks["hbm_gbs"]), "traffic": None, "kernel": "k_pauli_screen",
-                         "bytes_per_candidate": PAULI_SCREEN_BYTES_PER_CAND,
+                         "frac": gbs / float(peaks["hbm_gbs"]), "traffic": None, "kernel": "k_pauli_screen1",
+                         "bytes_per_candidate": nbytes / screened if screened else None,
                          "peak_source": f"hbm_gbs ({peak_src})",
-                         "note": "working set (basis, index) is L2-resident; latency-bound"},
+                         "note": "basis strings and index are L2-resident; only the flags reach HBM"},
             "e2e": {"value": cand / te, "unit": UNIT, "time_to_closure_s": te,
                     "h2d_bytes_per_step": int(s.nbytes + c.nbytes + o.nbytes),
                     "d2h_bytes_per_step": int(D * 16 + (D + 1) * 8)},

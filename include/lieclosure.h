@@ -296,7 +296,7 @@ LC_API int lie_closure_batched(int nsets, const lc_c128* const* generators, cons
  * max_dim    : capacity in elements (>= 1).
  * opt, rep   : as lie_closure; opt->precision is ignored (everything is FP64,
  *              exact for single-string sets), opt->block_k is the candidate
- *              block (0 = 2^20), opt->fault_inject = 2 starts the per-candidate
+ *              block (0 = 2^22), opt->fault_inject = 2 starts the per-candidate
  *              hash tables at their smallest size (a test hook that exercises
  *              the regrow path).
  * Report: brackets_checked, n_flagged, cursor and the residual margins as in

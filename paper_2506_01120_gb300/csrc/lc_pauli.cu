@@ -133,13 +133,30 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// FP64 issue is scarce on this part (each warp-wide FP64 instruction holds
+// the SM's FP64 pipe for many cycles), so the norms below spend FP64
+// instructions only where some lane holds a non-zero value; zero tests are
+// integer tests on the bit pattern.  Skipped terms are exact zeros, so the
+// sums are bit-for-bit those of the plain loop.
+__device__ __forceinline__ bool nonzero(double v) { return (__double_as_longlong(v) << 1) != 0; }
+
+// sum of per-lane partials; with at most one non-zero partial the result is
+// that partial, moved by a shuffle
+__device__ __forceinline__ double warp_sum_sparse(double v) {
+  const unsigned bal = __ballot_sync(kFull, nonzero(v));
+  if (bal == 0) return 0.0;
+  if ((bal & (bal - 1)) == 0) return __shfl_sync(kFull, v, __ffs(bal) - 1);
+  return warp_sum(v);
+}
+
 __device__ __forceinline__ double table_norm2(const Table& t, int lane) {
   double s = 0.0;
   for (uint32_t i = lane; i <= t.mask; i += 32) {
     const double v = t.val[i];
-    s = fma(v, v, s);
+    const bool nz = nonzero(v);
+    if (__any_sync(kFull, nz) && nz) s = fma(v, v, s);
   }
-  return warp_sum(s);
+  return warp_sum_sparse(s);
 }
 
 struct PBasis {
@@ -171,6 +188,7 @@ struct PState {
   int nflag, nnonzero, noverflow;   // screen counters of the current block
   int npure;         // flagged candidates that are one string absent from the basis
   int nfirst;        // distinct strings among them (first occurrences in pair order)
+  int nonunit;       // some one-term element has a coefficient other than +-1
 };
 
 // pair index t = l(l-1)/2 + m -> (l, m): a single-precision square root
@@ -249,7 +267,7 @@ __device__ bool project(const PBasis& B, int nrows, const Table& h, const Table&
   for (uint32_t i = lane; i <= h.mask; i += 32) {
     const u64 s = h.key[i];
     const double x = h.val[i];
-    if (s == kEmpty || x == 0.0) continue;
+    if (s == kEmpty || !nonzero(x)) continue;
     int e = index_head<RO>(B, s);
     for (int guard = 0; e >= 0 && guard < nrows; ++guard) {   // one term per element and string
       const int r = ld<RO>(&B.row[e]);
@@ -320,7 +338,7 @@ __global__ void __launch_bounds__(256) k_pauli_screen(PBasis B, long long t0, in
               int nnz = 0;
               for (uint32_t q0 = 0; q0 <= h.mask; q0 += 32) {
                 const uint32_t q = q0 + lane;
-                const bool on = h.key[q] != kEmpty && h.val[q] != 0.0;
+                const bool on = h.key[q] != kEmpty && nonzero(h.val[q]);
                 const unsigned bal = __ballot_sync(kFull, on);
                 if (on && nnz + __popc(bal & ((1u << lane) - 1u)) == 0) {
                   pkey[c] = h.key[q];
@@ -333,7 +351,7 @@ __global__ void __launch_bounds__(256) k_pauli_screen(PBasis B, long long t0, in
                 ++npure;
               }
             }
-          } else {
+          } else if (lane == 0 && nonzero(r2)) {
             maxrej = fmax(maxrej, sqrt(r2 / h2));
           }
         }
@@ -351,6 +369,53 @@ __global__ void __launch_bounds__(256) k_pauli_screen(PBasis B, long long t0, in
     if (nov) atomicAdd(&ps->noverflow, nov);
     if (npure) atomicAdd(&ps->npure, npure);
     if (maxrej > 0.0) atomicMax(&ps->max_screen_rej_bits, (unsigned long long)__double_as_longlong(maxrej));
+  }
+}
+
+// Screen for a basis whose every element is one string with coefficient
+// exactly +-1 (so element i owns term i): one thread per candidate.  A
+// bracket of two such elements is zero (commuting strings) or +-2 times the
+// product string; it is dependent exactly when that string is in the basis
+// (the residual c - (c v) v is then 0 with v = +-1) and otherwise pure.  The
+// flags, counters and pure records equal those of k_pauli_screen for such a
+// basis, with no FP64 arithmetic outside the pure records.
+__global__ void __launch_bounds__(256) k_pauli_screen1(PBasis B, long long t0, int count,
+                                                       unsigned char* __restrict__ flag,
+                                                       unsigned* __restrict__ chunks, u64* __restrict__ pkey,
+                                                       double* __restrict__ pval, PState* ps) {
+  int nz = 0, nf = 0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < count;
+       c += (long long)gridDim.x * blockDim.x) {
+    int l, m;
+    pair_of(t0 + c, &l, &m);
+    const u64 ka = __ldg(&B.key[l]), kb = __ldg(&B.key[m]);
+    const int g = pauli_phase(ka, kb);
+    unsigned char fl = 0;
+    if (g & 1) {
+      ++nz;
+      const u64 s = ka ^ kb;
+      if (index_head<true>(B, s) < 0) {
+        fl = 2;
+        ++nf;
+        const double cv = __ldg(&B.val[l]) * __ldg(&B.val[m]);
+        pkey[c] = s;
+        pval[c] = g == 1 ? -2.0 * cv : 2.0 * cv;
+        atomicOr(&chunks[c >> 15], 1u << ((c >> 10) & 31));
+      }
+    }
+    flag[c] = fl;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    nz += __shfl_xor_sync(kFull, nz, o);
+    nf += __shfl_xor_sync(kFull, nf, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (nz) atomicAdd(&ps->nnonzero, nz);
+    if (nf) {
+      atomicAdd(&ps->nflag, nf);
+      atomicAdd(&ps->npure, nf);
+    }
   }
 }
 
@@ -443,7 +508,7 @@ __device__ __forceinline__ int pure_take(const PState* ps, int n0, long long t0t
 __global__ void k_pure_append(PBasis B, const unsigned char* __restrict__ first, const u64* __restrict__ pkey,
                               const double* __restrict__ pval, int count, const int* __restrict__ coff,
                               int nchunks, int n0, long long t0terms, int ncap, long long tcap,
-                              const PState* ps) {
+                              PState* ps) {
   const int ch = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (ch >= nchunks) return;
   const int take = pure_take(ps, n0, t0terms, ncap, tcap);
@@ -459,9 +524,11 @@ __global__ void k_pure_append(PBasis B, const unsigned char* __restrict__ first,
         const double r2 = fma(v, v, 0.0);
         const long long pos = t0terms + i;
         const u64 s = pkey[c];
+        const double u = v * (1.0 / sqrt(r2));
         B.key[pos] = s;
-        B.val[pos] = v * (1.0 / sqrt(r2));
+        B.val[pos] = u;
         B.row[pos] = n0 + i;
+        if (u != 1.0 && u != -1.0) atomicOr(&ps->nonunit, 1);
         B.off[n0 + i + 1] = pos + 1;
         index_push(B, s, (int)pos);
       }
@@ -552,10 +619,12 @@ __global__ void __launch_bounds__(32, 1) k_pauli_accept(PBasis B, PSrc G, int ge
           const unsigned bal = __ballot_sync(kFull, keep);
           if (keep) {
             const long long pos = wpos + __popc(bal & ((1u << lane) - 1u));
+            const double u = v * inv;
             B.key[pos] = s;
-            B.val[pos] = v * inv;
+            B.val[pos] = u;
             B.row[pos] = N;
             pushed &= index_push(B, s, (int)pos);
+            if (cnt == 1 && u != 1.0 && u != -1.0) atomicOr(&ps->nonunit, 1);
           }
           wpos += __popc(bal);
         }
@@ -653,7 +722,8 @@ class ClosureP {
   ClosureP(int k, int nq, double tol, long long ncap, long long tcap, const lc_options& o, cudaStream_t s)
       : k_(k), nq_(nq), tol_(tol), ncap_(ncap), tcap_(tcap), opt_(o), s_(s) {
     eta_ = o.eta_abs > 0 ? o.eta_abs : 1e-12;
-    K_ = o.block_k > 0 ? o.block_k : (1 << 20);
+    K_ = o.block_k > 0 ? o.block_k : (1 << 22);
+    K_ = (int)std::max<long long>(1, std::min<long long>(K_, pairs_below(ncap)));   // no larger than the sweep
   }
   ~ClosureP() {
     for (cudaEvent_t& e : ev_)
@@ -748,7 +818,7 @@ class ClosureP {
   bool trace_ = false;
   long long N_ = 0, T_ = 0, t_ = 0, checked_ = 0, flagged_ = 0, nonzero_ = 0, blocks_ = 0, launches_ = 0;
   double t_start_ = 0.0, t_last_ = 0.0, t_screen_ = 0.0, t_accept_ = 0.0;
-  long long screens_ = 0;
+  long long screens_ = 0, screens1_ = 0;
   cudaEvent_t ev_[4] = {nullptr, nullptr, nullptr, nullptr};   // with opt.profile: screen, accept
 
   bool profiling() {
@@ -950,15 +1020,26 @@ class ClosureP {
       hs_->nflag = hs_->nnonzero = hs_->noverflow = hs_->npure = hs_->nfirst = 0;
       LP_TRY(cudaMemcpyAsync(&ps_->nflag, &hs_->nflag, 5 * sizeof(int), cudaMemcpyHostToDevice, s_));
       LP_TRY(cudaMemsetAsync(chunks_, 0, 4ull * ((count + 32767) / 32768 + 1), s_));
-      const int warps = std::max(1, std::min(8, (96 * 1024) / (16 * (hsl_ + bsl_))));
-      const size_t sm = 16ull * (hsl_ + bsl_) * warps;
-      LP_TRY(cudaFuncSetAttribute(k_pauli_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      const long long want = (count + warps - 1) / warps;
-      const int grid = (int)std::max<long long>(1, std::min<long long>(want, 8ll * nsm_));
+      // one-term elements with unit coefficients: the thread-per-candidate
+      // screen gives the same flags (needs ||h|| = 2 above the floor and a
+      // new string's relative residual 1 above tol / 2)
+      const bool unit1 = maxT_ == 1 && hs_->nonunit == 0 && eta_ < 2.0 && tol_ < 2.0;
       const bool prof = profiling();
-      if (prof) cudaEventRecord(ev_[0], s_);
-      k_pauli_screen<<<grid, 32 * warps, sm, s_>>>(B_, t_, count, (int)N_, hsl_, bsl_, tol_, eta_, flag_, chunks_,
-                                                   pkey_, pval_, ps_);
+      if (unit1) {
+        const int grid = (int)std::max<long long>(1, std::min<long long>((count + 255) / 256, 8ll * nsm_));
+        if (prof) cudaEventRecord(ev_[0], s_);
+        k_pauli_screen1<<<grid, 256, 0, s_>>>(B_, t_, count, flag_, chunks_, pkey_, pval_, ps_);
+        ++screens1_;
+      } else {
+        const int warps = std::max(1, std::min(8, (96 * 1024) / (16 * (hsl_ + bsl_))));
+        const size_t sm = 16ull * (hsl_ + bsl_) * warps;
+        LP_TRY(cudaFuncSetAttribute(k_pauli_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        const long long want = (count + warps - 1) / warps;
+        const int grid = (int)std::max<long long>(1, std::min<long long>(want, 8ll * nsm_));
+        if (prof) cudaEventRecord(ev_[0], s_);
+        k_pauli_screen<<<grid, 32 * warps, sm, s_>>>(B_, t_, count, (int)N_, hsl_, bsl_, tol_, eta_, flag_,
+                                                     chunks_, pkey_, pval_, ps_);
+      }
       if (prof) cudaEventRecord(ev_[1], s_);
       ++screens_;
       ++launches_;
