@@ -1,6 +1,6 @@
 // Host driver and C ABI of the Lie-closure library.
 //
-// The driver runs Algorithm 4 of arXiv 2506.01120 (Section 3.2) in candidate
+// This host code runs Algorithm 4 of arXiv 2506.01120 (Section 3.2) in candidate
 // blocks.  The basis V lives on the device as packed FP64 rows (see
 // lc_internal.cuh); a block is a contiguous run of the pair sweep
 // (l, m), m < l, l ascending then m ascending, restricted to l < |V| at the
