@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--pauli-qubits", type=int, nargs="*", default=[6, 7],
                     help="qubit counts of the sparse hardware-efficient-ansatz workloads")
     ap.add_argument("--pauli-only", action="store_true", help="run only the sparse Pauli-sum leg")
+    ap.add_argument("--next-rows", action="store_true",
+                    help="run only the Algorithm 2 / Algorithm 3 / resume timings and print them as one line")
     return ap.parse_args()
 
 
@@ -287,6 +289,51 @@ def pauli_leg(args, stream, peaks, peak_src):
     return out
 
 
+def next_rows_leg():
+    """Algorithm 3 on the su(64) chain (mixed, host API), Algorithm 2 against
+    Algorithm 4 in FP64 (full sweeps), and an su(64) closure stopped halfway
+    and resumed."""
+    from paper_2506_01120_gb300 import binding, inputs
+    out = {}
+    g, _ = inputs.workload_generators(WORKLOAD)
+    binding.lie_closure(g, 1e-8, return_basis=False)          # warm the library and pool
+    t0 = time.perf_counter()
+    B, V, st, rep = binding.lie_closure_alg3(g, 1e-8, precision="mixed")
+    t = time.perf_counter() - t0
+    cand = rep["brackets_checked"] + rep["generators_checked"]
+    out["alg3_su64_chain_d64_mixed"] = {"dim": len(V), "candidates": cand, "time_to_closure_s": t,
+                                        "brackets_per_s": cand / t, "status": st}
+    # Algorithm 2 against Algorithm 4 (both FP64): the su(2^n) chains, whose
+    # Gram matrix stays the identity, and a random traceless pair, where the
+    # paper warns that the inverse can go unstable
+    cases = [(f"su{2 ** n}_chain_d{2 ** n}", inputs.generators_from_labels(inputs.su2n_chain_labels(n)))
+             for n in (4, 5)]
+    cases.append(("random2_d16", inputs.random_set(16, 2, seed=116)))
+    for label, gr in cases:
+        row = {}
+        for name, fn in (("alg4_fp64", lambda: binding.lie_closure(gr, 1e-8, precision="fp64", check=False)),
+                         ("alg2_fp64", lambda: binding.lie_closure_alg2(gr, 1e-8, check=False))):
+            t0 = time.perf_counter()
+            r = fn()
+            t = time.perf_counter() - t0
+            c = r.report["brackets_checked"] + r.report["generators_checked"]
+            row[name] = {"dim": r.dim, "status": binding.status_string(r.status), "candidates": c,
+                         "time_to_closure_s": t, "brackets_per_s": c / t}
+        out[label] = row
+    full = binding.lie_closure(g, 1e-8, precision="mixed")
+    half = full.report["brackets_checked"] // 2
+    t0 = time.perf_counter()
+    a = binding.lie_closure(g, 1e-8, precision="mixed", max_candidates=half)
+    t1 = time.perf_counter()
+    b = binding.lie_closure_resume(a.basis, (a.report["cursor_l"], a.report["cursor_m"]), 1e-8, precision="mixed")
+    t2 = time.perf_counter()
+    import numpy as np
+    out["resume_su64_chain_d64_mixed"] = {
+        "full_time_s": full.report["t_total_s"], "first_half_s": t1 - t0, "resumed_half_s": t2 - t1,
+        "same_basis": bool(b.dim == full.dim and np.abs(b.basis - full.basis).max() < 1e-12)}
+    return out
+
+
 def run_ours(args, world, rank, local, pg):
     import numpy as np
     import torch
@@ -298,6 +345,10 @@ def run_ours(args, world, rank, local, pg):
     if rank == 0 and not os.path.exists(binding.LIB_PATH):
         build()
     barrier(pg)
+    if args.next_rows:
+        if rank == 0:
+            print(json.dumps({"next_rows": next_rows_leg()}), flush=True)
+        return
     if args.pauli_only:
         peaks, peak_src = measured_peaks()
         sp = pauli_leg(args, torch.cuda.current_stream(), peaks, peak_src)

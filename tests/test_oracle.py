@@ -337,3 +337,16 @@ def test_packed_pauli_strings_follow_the_oracle_bit_convention():
         ref = inputs.pauli_matrix(oc.bits_to_pauli(x, z, 2))
         ratio = prod[np.nonzero(ref)] / ref[np.nonzero(ref)]
         assert np.allclose(ratio, ratio[0]) and abs(abs(ratio[0]) - 1) < 1e-15
+
+
+def test_alg2_goes_unstable_where_alg4_does_not():
+    """Section 3.1 warns that the matrix-inversion method may be numerically
+    unstable.  On a random traceless pair at d = 16 and tol = 1e-8 Algorithm 4
+    returns su(16) (255, the closed form) while Algorithm 2's inverse Gram
+    matrix lets rounding through and its basis grows past any possible
+    dimension (capacity 2 d^2 reached)."""
+    from paper_2506_01120_gb300 import inputs
+    g = inputs.random_set(16, 2, seed=116)
+    assert oc.alg4_orthonormalization(g, 1e-8, saturation_exit=True).dim == 255
+    with pytest.raises(oc.CapacityError):
+        oc.alg2_matrix_inversion(g, 1e-8)
