@@ -433,6 +433,12 @@ def run_ours(args, world, rank, local, pg):
                "time_to_closure_s": e2e_t / len(walls)}
 
     # the plain FP64 GPU form against the mixed form on the same prefix
+    # the same closure with the (optional, not in the paper) saturation exit,
+    # labelled separately: it stops once |V| reaches d^2 - 1
+    rs = binding.lie_closure_dev(gd, tol, stream=stream, precision="mixed", saturation_exit=1)
+    sat = {"dim": rs.dim, "candidates": rs.report["brackets_checked"] + rs.report["generators_checked"],
+           "time_to_closure_s": rs.report["t_total_s"]}
+
     fp64 = None
     if args.fp64_prefix > 0:
         rf = binding.lie_closure_dev(gd, tol, stream=stream, precision="fp64", max_candidates=args.fp64_prefix)
@@ -473,6 +479,7 @@ def run_ours(args, world, rank, local, pg):
                      "kernel": "k_split_gemm (projection + residual)", "launches_per_step": gemm_n / args.steps,
                      "peak_source": f"bf16_tflops_sustained ({peak_src})"},
         "e2e": e2e,
+        "saturation_exit": sat,
         "fp64_gpu": fp64,
         "sparse_pauli": sparse,
         "cpu_baseline": cpu,
