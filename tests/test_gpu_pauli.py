@@ -10,6 +10,9 @@ generators; the GPU path never forms a matrix.  Bars:
   +-1, and the set of strings equals the exact Pauli closure (O3);
 * the basis is orthonormal in the coefficient inner product within 1e-12.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -18,6 +21,8 @@ from paper_2506_01120_gb300 import binding, inputs
 from paper_2506_01120_gb300.build import build
 
 pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_dims.json")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -164,6 +169,9 @@ def test_hea_full_size(n):
     coefficient +-1, every pair of the final basis checked."""
     res = run(labels_ops(inputs.su2n_chain_labels(n)), n, 1e-8)
     D = 4 ** n - 1
+    with open(GOLDEN) as fh:
+        t2 = json.load(fh)["table2_hea_sparse"]
+    assert t2["dim"][t2["n"].index(n)] == D          # the dimensions Table 2 prints
     assert res.dim == D
     assert res.status == binding.LC_OK
     assert res.report["brackets_checked"] == D * (D - 1) // 2
