@@ -37,13 +37,16 @@ LC_API int lc_split_gemm_f32(const float* A, const float* B, int M, int N, int K
  * free device memory, code under a hard memory cap, or a path where
  * cudaMalloc/cudaFree (which may synchronise the device) is not allowed.
  *
- * Arguments, result and error codes are those of lc_split_gemm_f32.  The
- * workspace is one fixed 32 MiB array in device global memory, created on
- * every GPU that loads the library and kept until the process exits.  The
- * padded problem must fit in it: 4 (Mp Kp + Np Kp) + 4 Mp Np bytes plus a
- * little alignment, with Mp = M rounded up to 128, Np = N rounded up to 256
- * and Kp = K rounded up to 32 (for example M = N = K = 1024 fits); larger
- * problems return LC_ERR_TOO_LARGE without touching the GPU.
+ * Arguments and result are those of lc_split_gemm_f32.  The workspace is one
+ * fixed 32 MiB array in device global memory, created on every GPU that loads
+ * the library and kept until the process exits.  The padded problem must fit
+ * in it: 4 (Mp Kp + Np Kp) + 4 Mp Np bytes plus a little alignment, with
+ * Mp = M rounded up to 128, Np = N rounded up to 256 and Kp = K rounded up to
+ * 32 (for example M = N = K = 1024 fits); larger problems return
+ * LC_ERR_TOO_LARGE without touching the GPU.
+ * Returns LC_OK, LC_ERR_ARG (null pointer or an extent < 1),
+ * LC_ERR_TOO_LARGE, LC_ERR_CUDA or LC_ERR_TIMEOUT; never LC_ERR_OOM, since it
+ * allocates nothing.
  * The first call on a device looks up the array's device address with that
  * device current; make that first call before any stream capture.
  * All calls share the one array and it keeps the last call's contents; the

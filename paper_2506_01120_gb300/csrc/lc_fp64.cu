@@ -700,15 +700,22 @@ cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2
                        int ldv, int ncap, int P, DevStats* stats, DevStatus* st, unsigned int* bar, long long spin_cap,
                        cudaStream_t s, int phantom, const double* Hraw, double* Bk, double* bn2) {
   if (f <= 0) return cudaSuccess;
-  static std::once_flag once;
-  static int nblocks = 1;
-  std::call_once(once, [] {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_accept_seq, 256, 0);
-    nblocks = std::max(1, std::min(sms, sms * per));
-  });
+  // co-resident CTAs of the cooperative launch, per device
+  static std::mutex mu;
+  static int per_dev[128] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+  int nblocks;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (!per_dev[dev]) {
+      int per = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_accept_seq, 256, 0);
+      const int sms = device_sm_count();
+      per_dev[dev] = std::max(1, std::min(sms, sms * per));
+    }
+    nblocks = per_dev[dev];
+  }
   const int G = std::max(1, std::min(nblocks, f));
   uint64_t lim = spin_cap > 0 ? (uint64_t)spin_cap : 4000000000ull;
   void* args[] = {&f,   &R,     &ldr,   &rn2, (void*)&hn2, &tol,    &eta2,          &V,  &ldv, &ncap, &P,

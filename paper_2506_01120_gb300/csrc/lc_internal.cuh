@@ -17,6 +17,9 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 #include <cstddef>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "../../include/lieclosure.h"
 
@@ -63,6 +66,38 @@ inline long long pairs_below(long long n) { return n * (n - 1) / 2; }
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 inline long long round_up_ll(long long x, long long m) { return (x + m - 1) / m * m; }
+
+// Dynamic shared memory above 48 KB is an opt-in attribute of a kernel in
+// one device's context, so it is set once per (kernel, device, size) with the
+// device current, not once per process.
+inline cudaError_t smem_optin(const void* kernel, int bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<std::pair<const void*, int>, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> g(mu);
+  const auto key = std::make_pair(std::make_pair(kernel, dev), bytes);
+  if (done.count(key)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.insert(key);
+  return e;
+}
+
+// Multiprocessor count of the current device (cached per device).
+inline int device_sm_count() {
+  static std::mutex mu;
+  static int cache[128] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return 1;
+  std::lock_guard<std::mutex> g(mu);
+  if (!cache[dev]) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = sms > 0 ? sms : 1;
+  }
+  return cache[dev];
+}
 
 // ------------------------------------------------------------ FP64 kernels
 // (lc_fp64.cu)

@@ -434,11 +434,7 @@ cudaError_t split_gemm_tcgen05(const SplitGemmArgs& a, cudaStream_t s) {
   if (!make_map(&mAhi, a.Ahi, a.M, a.K, a.lda, BM, G::BK) || !make_map(&mAlo, a.Alo, a.M, a.K, a.lda, BM, G::BK) ||
       !make_map(&mBhi, a.Bhi, a.N, a.K, a.ldb, G::BN, G::BK) || !make_map(&mBlo, a.Blo, a.N, a.K, a.ldb, G::BN, G::BK))
     return cudaErrorInvalidValue;
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_split_gemm<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
-  });
+  const cudaError_t attr_err = smem_optin(reinterpret_cast<const void*>(k_split_gemm<G>), G::SMEM);
   if (attr_err != cudaSuccess) return attr_err;
   GemmParams p;
   p.M = a.M;
@@ -710,11 +706,7 @@ cudaError_t launch_bracket_tc(const __nv_bfloat16* Ehi, const __nv_bfloat16* Elo
   if (!make_map(&mh, Ehi, nrows_elems * C::R, C::R, C::R, C::R) ||
       !make_map(&ml, Elo, nrows_elems * C::R, C::R, C::R, C::R))
     return cudaErrorInvalidValue;
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_bracket_tc<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-  });
+  const cudaError_t attr_err = smem_optin(reinterpret_cast<const void*>(k_bracket_tc<D>), C::SMEM);
   if (attr_err != cudaSuccess) return attr_err;
   const uint64_t lim = spin_cap > 0 ? (uint64_t)spin_cap : 4000000000ull;
   k_bracket_tc<D><<<count, 128, C::SMEM, s>>>(mh, ml, t0, Hhi, Hlo, ldh, hn2, lim, st);
@@ -780,15 +772,33 @@ extern "C" LC_API int lc_split_gemm_f32_noalloc(const float* A, const float* B, 
   using namespace lc;
   if (!A || !B || !D || M < 1 || N < 1 || K < 1) return LC_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const size_t Mp = (size_t)round_up(M, BM), Np = (size_t)round_up(N, ScreenCfg::BN),
-               Kp = (size_t)round_up(K, ScreenCfg::BK);
-  // layout inside the scratch array, every region 256-byte aligned
-  size_t off = 0;
-  auto place = [&](size_t bytes) { const size_t at = off; off = (off + bytes + 255) & ~size_t(255); return at; };
-  const size_t oAhi = place(Mp * Kp * 2), oAlo = place(Mp * Kp * 2);
-  const size_t oBhi = place(Np * Kp * 2), oBlo = place(Np * Kp * 2);
-  const size_t oD = place(Mp * Np * 4), oSt = place(sizeof(DevStatus));
-  if (off > kNoAllocScratchBytes) return LC_ERR_TOO_LARGE;
+  // Every padded extent is at least one tile, and the output alone takes
+  // 4 Mp Np bytes, so no extent above the array size in elements can fit;
+  // rejecting those first keeps the sizing arithmetic below far from overflow.
+  const long long lim = (long long)(kNoAllocScratchBytes / 4);
+  if ((long long)M > lim || (long long)N > lim || (long long)K > lim) return LC_ERR_TOO_LARGE;
+  const unsigned long long Mp = (unsigned long long)round_up_ll(M, BM),
+                           Np = (unsigned long long)round_up_ll(N, ScreenCfg::BN),
+                           Kp = (unsigned long long)round_up_ll(K, ScreenCfg::BK);
+  // layout inside the scratch array, every region 256-byte aligned; each
+  // region is checked against the remaining room before it is added
+  unsigned long long off = 0;
+  bool fits = true;
+  auto place = [&](unsigned long long bytes) {
+    const unsigned long long at = off;
+    if (!fits || bytes > kNoAllocScratchBytes - off) {
+      fits = false;
+      return at;
+    }
+    off = (off + bytes + 255) & ~255ull;
+    if (off > kNoAllocScratchBytes) fits = false;
+    return at;
+  };
+  // the products below are at most lim^2 * 4 < 2^62: no wrap
+  const unsigned long long oAhi = place(Mp * Kp * 2), oAlo = place(Mp * Kp * 2);
+  const unsigned long long oBhi = place(Np * Kp * 2), oBlo = place(Np * Kp * 2);
+  const unsigned long long oD = place(Mp * Np * 4), oSt = place(sizeof(DevStatus));
+  if (!fits) return LC_ERR_TOO_LARGE;
   if (!tcgen05_available()) return LC_ERR_CUDA;
   void* base = nullptr;
   if (noalloc_scratch_address(&base) != cudaSuccess) return LC_ERR_CUDA;
@@ -977,11 +987,7 @@ cudaError_t bracket_q64(const __nv_bfloat16* Qhi, const __nv_bfloat16* Qlo, long
   CUtensorMap mh, ml;
   if (!make_map(&mh, Qhi, nelems * 2 * Q_D, Q_D, Q_D, Q_D) || !make_map(&ml, Qlo, nelems * 2 * Q_D, Q_D, Q_D, Q_D))
     return cudaErrorInvalidValue;
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_bracket_q64, cudaFuncAttributeMaxDynamicSharedMemorySize, Q_SMEM);
-  });
+  const cudaError_t attr_err = smem_optin(reinterpret_cast<const void*>(k_bracket_q64), Q_SMEM);
   if (attr_err != cudaSuccess) return attr_err;
   const uint64_t lim = spin_cap > 0 ? (uint64_t)spin_cap : 4000000000ull;
   k_bracket_q64<<<count, 128, Q_SMEM, s>>>(mh, ml, t0, Hhi, Hlo, ldh, hn2, lim, st);
@@ -1167,11 +1173,7 @@ cudaError_t bracket_big(const __nv_bfloat16* Ehi, const __nv_bfloat16* Elo, long
   if (!make_map(&ah, Ehi, nelems * R, R, R, 64) || !make_map(&al, Elo, nelems * R, R, R, 64) ||
       !make_map(&bh, Ehi, nelems * R, R, R, BN) || !make_map(&bl, Elo, nelems * R, R, R, BN))
     return cudaErrorInvalidValue;
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_bracket_big, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  });
+  const cudaError_t attr_err = smem_optin(reinterpret_cast<const void*>(k_bracket_big), SMEM_BYTES);
   if (attr_err != cudaSuccess) return attr_err;
   cudaError_t e = cudaMemsetAsync(hn2, 0, sizeof(float) * count, s);
   if (e != cudaSuccess) return e;
