@@ -110,12 +110,14 @@ def test_tfim_sums_match_oracle_elementwise(n):
                                                 (4, 3, 2, 8, False), (5, 3, 2, 10, False), (3, 2, 4, 6, True),
                                                 (4, 2, 4, 13, True), (4, 2, 6, 15, True)])
 def test_random_sums_match_oracle_elementwise(n, k, terms, seed, sat):
-    """Random sums on both sides with the absolute floor eta_abs = 1e-9: chains
-    of accepts with small relative residuals amplify the dense oracle's
-    rounding, and a bracket that is zero can come out near 1e-11 there."""
+    """Random sums on both sides with the oracle's documented floor for Pauli
+    sums (oc.ETA_ABS_PAULI_SUMS = 1e-9): chains of accepts with small relative
+    residuals amplify the dense oracle's rounding, and a bracket that is zero
+    can come out near 1e-11 there."""
     ops = inputs.random_pauli_sums(n, k, terms, seed)
-    res = run(ops, n, 1e-8, saturation_exit=int(sat), eta_abs=1e-9)
-    check_elementwise(res, ops, n, 1e-8, saturation_exit=sat, eta_abs=1e-9)
+    eta = oc.ETA_ABS_PAULI_SUMS
+    res = run(ops, n, 1e-8, saturation_exit=int(sat), eta_abs=eta)
+    check_elementwise(res, ops, n, 1e-8, saturation_exit=sat, eta_abs=eta)
 
 
 def test_structural_zero_brackets_stay_zero():
@@ -129,7 +131,7 @@ def test_structural_zero_brackets_stay_zero():
     ops = inputs.random_pauli_sums(4, 2, 3, 14)
     res = run(ops, 4, 1e-8, saturation_exit=1)
     assert res.dim == 36
-    ref = oc.alg4_orthonormalization(dense(ops, 4), 1e-8, eta_abs=1e-9, saturation_exit=True)
+    ref = oc.alg4_orthonormalization(dense(ops, 4), 1e-8, eta_abs=oc.ETA_ABS_PAULI_SUMS, saturation_exit=True)
     assert ref.dim == 36
     # the oracle's later elements carry that compounded rounding (~2e-11)
     np.testing.assert_allclose(matrices(res, 4), ref.basis, atol=1e-9, rtol=0)

@@ -350,3 +350,137 @@ def test_alg2_goes_unstable_where_alg4_does_not():
     assert oc.alg4_orthonormalization(g, 1e-8, saturation_exit=True).dim == 255
     with pytest.raises(oc.CapacityError):
         oc.alg2_matrix_inversion(g, 1e-8)
+
+
+# -------------------------------------------- pins of the comparison metrics
+# The tests of the GPU path lean on ortho_defect, closure_residual and
+# margin_report as upper-bound gates, so each must recover a value planted in
+# its input; a metric that always returns 0 (or drops a term) fails here.
+def _tilted_su2(phi):
+    """{iXI, iYI, i(cos phi ZI + sin phi IX)}: orthonormal.  [iXI, iYI] = -2i ZI
+    has the component -2 cos(phi) along the third element, so its residual is
+    2 |sin phi| out of a norm of 2; the other two brackets are multiples of iYI
+    and iXI (in the span).  Closure residual: |sin phi| exactly."""
+    a, b, z, x = inputs.generators_from_labels(["XI", "YI", "ZI", "IX"])
+    return np.stack([a, b, np.cos(phi) * z + np.sin(phi) * x])
+
+
+def _overlap_basis(eps, phase, delta):
+    """Four orthonormal Pauli elements with element 1 tilted to overlap
+    eps * e^{i phase} with element 0 (still unit norm) and element 3 scaled by
+    (1 + delta): defect max(eps, 2 delta + delta^2)."""
+    V = inputs.generators_from_labels(["XI", "ZI", "IY", "ZZ"]).copy()
+    V[1] = np.sqrt(1 - eps ** 2) * V[1] + eps * np.exp(1j * phase) * V[0]
+    V[3] = (1 + delta) * V[3]
+    return V
+
+
+def _metric_pins_pass():
+    try:
+        for eps, phase, delta in [(1e-3, 0.0, 0.0), (2e-7, 1.1, 0.0), (1e-9, 2.5, 3e-6), (0.25, -0.4, 1e-4)]:
+            want = max(eps, 2 * delta + delta ** 2)
+            if abs(oc.ortho_defect(_overlap_basis(eps, phase, delta)) - want) > 1e-15 + 1e-9 * want:
+                return False
+        if oc.ortho_defect(inputs.generators_from_labels(oc.pauli_closure(["XY", "ZI"]))) > 1e-15:
+            return False
+        for phi in (0.3, 1e-4, 1.2):
+            if abs(oc.closure_residual(_tilted_su2(phi)) - abs(np.sin(phi))) > 1e-12:
+                return False
+        if oc.closure_residual(_tilted_su2(0.0)) > 1e-15:
+            return False
+        labels = oc.pauli_closure(inputs.so2n_chain_labels(3))
+        V = inputs.generators_from_labels(labels)
+        if oc.closure_residual(V) > 1e-15:          # so(6) is closed
+            return False
+        # so(6) minus one element: some pair brackets exactly onto the missing string
+        if abs(oc.closure_residual(V[:-1]) - 1.0) > 1e-12:
+            return False
+        # margins of a hand-built result
+        r = oc.Alg4Result(V=V, dim=3, accepted_rel=[0.5, 1e-3, 0.9], rejected_rel=[1e-14, 3e-12, 2e-13])
+        m = oc.margin_report(r)
+        if (m["min_acc_rel_res"], m["max_rej_rel_res"], m["n_acc"], m["n_rej_nonzero"]) != (1e-3, 3e-12, 3, 3):
+            return False
+        m0 = oc.margin_report(oc.Alg4Result(V=V, dim=0))
+        if not (m0["min_acc_rel_res"] == np.inf and m0["max_rej_rel_res"] == 0.0):
+            return False
+        # margins of a real run: the second generator iXI + eps iZZ has relative
+        # residual eps / sqrt(1 + eps^2) against the first
+        eps = 1e-3
+        a, zz = inputs.generators_from_labels(["XI", "ZZ"])
+        res = oc.alg4_orthonormalization(np.stack([a, a + eps * zz]), 1e-8)
+        mr = oc.margin_report(res)
+        if abs(mr["min_acc_rel_res"] - eps / np.sqrt(1 + eps ** 2)) > 1e-12:
+            return False
+        if mr["n_acc"] != res.dim or mr["max_rej_rel_res"] > 1e-12:
+            return False
+        return True
+    except Exception:
+        return False
+
+
+def test_metric_pins_pass_unpatched():
+    assert _metric_pins_pass()
+
+
+def test_ortho_defect_recovers_planted_overlap():
+    for eps in (1e-12, 1e-6, 0.1):
+        assert oc.ortho_defect(_overlap_basis(eps, 0.7, 0.0)) == pytest.approx(eps, rel=1e-9, abs=1e-16)
+    assert oc.ortho_defect(_overlap_basis(0.0, 0.0, 1e-5)) == pytest.approx(2e-5 + 1e-10, rel=1e-9)
+
+
+def test_closure_residual_recovers_planted_tilt():
+    for phi in (1e-6, 0.3, np.pi / 2):
+        assert oc.closure_residual(_tilted_su2(phi)) == pytest.approx(abs(np.sin(phi)), rel=1e-10, abs=1e-15)
+    # the pair list restricts the maximum: only (1, 0) leaves the span
+    V = _tilted_su2(0.5)
+    assert oc.closure_residual(V, pairs=[(2, 0), (2, 1)]) < 1e-15
+    assert oc.closure_residual(V, pairs=[(1, 0)]) == pytest.approx(np.sin(0.5), rel=1e-12)
+
+
+def test_margin_report_of_a_near_dependent_generator():
+    for eps in (1e-2, 1e-5):
+        a, zz = inputs.generators_from_labels(["XI", "ZZ"])
+        res = oc.alg4_orthonormalization(np.stack([a, a + eps * zz]), 1e-8)
+        m = oc.margin_report(res)
+        assert m["min_acc_rel_res"] == pytest.approx(eps / np.sqrt(1 + eps ** 2), rel=1e-10)
+        assert m["n_acc"] == res.dim
+
+
+@pytest.mark.parametrize("mistake", ["defect_zero", "defect_signed", "defect_no_identity", "residual_unscaled",
+                                     "residual_anticommutator", "residual_no_projection", "margin_swapped",
+                                     "margin_first_accept"])
+def test_planted_metric_mistake_is_caught(monkeypatch, mistake):
+    """Each plausible slip in a comparison metric makes a metric pin fail."""
+    if mistake == "defect_zero":
+        monkeypatch.setattr(oc, "ortho_defect", lambda V: 0.0)
+    elif mistake == "defect_signed":
+        monkeypatch.setattr(oc, "ortho_defect",
+                            lambda V: float(np.max((oc.gram(V) - np.eye(V.shape[0])).real)) if len(V) else 0.0)
+    elif mistake == "defect_no_identity":
+        monkeypatch.setattr(oc, "ortho_defect",
+                            lambda V: float(np.max(np.abs(oc.gram(V) - np.diag(np.diag(oc.gram(V)))))))
+    elif mistake == "residual_unscaled":
+        def unscaled(V, pairs=None, eta_abs=1e-12):
+            N = V.shape[0]
+            pairs = pairs or [(i, j) for i in range(N) for j in range(i)]
+            return max([oc.norm(oc.project_out(V, oc.bracket(V[i], V[j]))) for i, j in pairs] or [0.0])
+        monkeypatch.setattr(oc, "closure_residual", unscaled)
+    elif mistake == "residual_anticommutator":
+        monkeypatch.setattr(oc, "bracket", lambda a, b: a @ b + b @ a)
+    elif mistake == "residual_no_projection":
+        monkeypatch.setattr(oc, "project_out", lambda V, h: h.copy())
+    elif mistake == "margin_swapped":
+        orig = oc.margin_report
+        def swapped(res):
+            m = orig(res)
+            m["min_acc_rel_res"], m["max_rej_rel_res"] = m["max_rej_rel_res"], m["min_acc_rel_res"]
+            return m
+        monkeypatch.setattr(oc, "margin_report", swapped)
+    elif mistake == "margin_first_accept":
+        orig = oc.margin_report
+        def first(res):
+            m = orig(res)
+            m["min_acc_rel_res"] = res.accepted_rel[0] if res.accepted_rel else np.inf
+            return m
+        monkeypatch.setattr(oc, "margin_report", first)
+    assert not _metric_pins_pass()
