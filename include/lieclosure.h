@@ -66,12 +66,25 @@ typedef enum {
   LC_PREC_MIXED_BF16X3 = 1
 } lc_precision;
 
+typedef enum {
+  /* accept iff ||h - proj_V h|| > tol * ||h|| (default) */
+  LC_TOL_RELATIVE = 0,
+  /* accept iff ||h - proj_V h|| > tol (elements of V have unit norm, so this
+     is the literal "h_perp != 0" of Algorithm 4 with an absolute threshold) */
+  LC_TOL_ABSOLUTE = 1
+} lc_tol_mode;
+
 typedef struct {
   int precision;              /* lc_precision; default LC_PREC_MIXED_BF16X3 */
   double eta_abs;             /* absolute floor on ||h||; default 1e-12 */
   double tau_screen;          /* mixed mode: relative residual below which a
                                  screened candidate is rejected without the FP64
-                                 recheck; 0 = default (1e-3) */
+                                 recheck.  0 (default) = measured: tau_screen =
+                                 screen_kappa * eps_screen, where eps_screen is
+                                 the largest screened relative residual of
+                                 probe vectors that lie in span(V) (true
+                                 residual 0), re-measured whenever |V| has grown
+                                 by 1/8; clamped to [2^-21, 1e-3] */
   int block_k;                /* candidates per block once the basis stops
                                  growing; 0 = automatic (16384 mixed, 2048 FP64,
                                  capped by an 8 GB buffer budget) */
@@ -93,6 +106,26 @@ typedef struct {
                                  for an arrival that never comes, so its bounded
                                  wait runs out (spin_cap) and the call returns
                                  LC_ERR_TIMEOUT with the device still usable */
+  int tol_mode;               /* lc_tol_mode; default LC_TOL_RELATIVE (dense
+                                 paths; lie_closure_alg2 and lie_closure_pauli
+                                 ignore it) */
+  int autotune;               /* mixed mode, nonzero: the first blocks after the
+                                 basis stops growing try screening-GEMM tile
+                                 shapes and block sizes on the real candidates,
+                                 time them with CUDA events and keep the fastest
+                                 for the rest of the call; the choice is cached
+                                 per (device, d, Algorithm 3 or 4) and reused by
+                                 later calls without trials.  Any choice gives
+                                 the same basis (blocking does not change the
+                                 decisions).  Default 0: fixed defaults */
+  int ortho_check;            /* nonzero: before returning, compute
+                                 rep->ortho_defect = max |<v_i, v_j> - delta_ij|
+                                 in FP64 on the device, over all rows when
+                                 |V| <= 4096, else over every q-th row with
+                                 q = ceil(|V| / 4096).  Default 0 (the report
+                                 field is then -1) */
+  double screen_kappa;        /* factor of the measured tau_screen; 0 =
+                                 default (10) */
 } lc_options;
 
 typedef struct {
@@ -122,6 +155,25 @@ typedef struct {
                                  3 screen, 4 FP64 accept, 5 other */
   int precision;
   int status;
+  long long n_gray;           /* mixed: screen rejects whose screened relative
+                                 residual lay in (eps_screen, tau_screen], the
+                                 band where the screen cannot tell a small true
+                                 residual from its own noise */
+  double eps_screen;          /* mixed: measured noise floor of the screen (the
+                                 largest value over the run's probes) */
+  double min_acc_screen_rel_res; /* mixed: smallest screened relative residual
+                                 among candidates that were then accepted
+                                 (their margin above tau_screen) */
+  double ortho_defect;        /* with opt.ortho_check: max |<v_i, v_j> -
+                                 delta_ij| over the checked rows, else -1 */
+  long long ortho_rows;       /* rows in that check */
+  int block_k_used;           /* saturated-phase block size used */
+  int block_k_growth_used;    /* growth-phase block size used */
+  int gemm_tile_n;            /* screening GEMM tile (128 x gemm_tile_n output, */
+  int gemm_tile_k;            /*   gemm_tile_k-wide k-slices) */
+  int autotuned;              /* 1 if block_k_used and the tile came from the
+                                 autotuner (trials in this call or its cache) */
+  int autotune_trials;        /* trial blocks this call spent */
 } lc_report;
 
 /* Fills *opt with the defaults listed above. */
@@ -261,6 +313,20 @@ LC_API int lie_closure_batched(int nsets, const lc_c128* const* generators, cons
                         const int* d, double tol, lc_c128* const* basis_out,
                         const long long* max_dim, long long* dim_out, int* status_out,
                         const lc_options* opt, lc_report* rep);
+
+/*
+ * lie_closure_batched_dev -- as lie_closure_batched with device buffers and a
+ * stream.  generators[s] and basis_out[s] are device pointers of the current
+ * device (the arrays of pointers themselves, k, d, max_dim, dim_out,
+ * status_out and rep are host memory); basis_out or basis_out[s] may be NULL.
+ * The sets run concurrently on streams of the library's own, ordered after the
+ * work already queued on `stream` (cudaStream_t as void*, NULL = legacy
+ * default stream); the call returns when every set is done.
+ */
+LC_API int lie_closure_batched_dev(int nsets, const lc_c128* const* generators, const int* k,
+                            const int* d, double tol, lc_c128* const* basis_out,
+                            const long long* max_dim, long long* dim_out, int* status_out,
+                            const lc_options* opt, lc_report* rep, void* stream);
 
 /*
  * lie_closure_pauli -- Algorithm 4 (Section 3.2) on operators held as sparse

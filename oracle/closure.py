@@ -35,6 +35,9 @@ Readings of the paper taken here (the paper leaves them open):
   is idempotent).
 * "h_perp != 0" is decided as ||h|| > eta_abs and ||h_perp|| > tol * ||h||,
   with h_perp from two classical Gram-Schmidt passes ("twice is enough").
+* ``tol_mode="absolute"`` reads the test as ||h_perp|| > tol instead (the
+  elements of V have unit norm, so this thresholds the orthogonal part
+  itself); the relative form is the default.
 * Optional saturation exit: for anti-Hermitian inputs the closure lies in
   su(d) plus at most one trace direction, so once |V| reaches that bound every
   remaining candidate is dependent.  Off by default.
@@ -128,8 +131,12 @@ class Alg4Result:
 
 
 def _test_and_append(n: int, h: np.ndarray, tol: float, eta_abs: float,
-                     res: Alg4Result) -> int:
-    """One independence check of Algorithm 4; returns the new |V| (res.V grows)."""
+                     res: Alg4Result, tol_mode: str = "relative") -> int:
+    """One independence check of Algorithm 4; returns the new |V| (res.V grows).
+
+    "h_perp != 0" is read as ||h_perp|| > tol * ||h|| (tol_mode "relative",
+    the default) or as ||h_perp|| > tol ("absolute": V has unit-norm elements,
+    so the threshold is on the orthogonal part itself)."""
     V = res.V
     hn = norm(h)
     res.candidates += 1
@@ -143,7 +150,7 @@ def _test_and_append(n: int, h: np.ndarray, tol: float, eta_abs: float,
     r = project_out(Vn, r)          # second pass
     rn = norm(r)
     rel = rn / hn
-    if rel > tol:
+    if (rn > tol) if tol_mode == "absolute" else (rel > tol):
         if n >= res.max_dim:
             raise CapacityError(f"closure dimension would exceed {res.max_dim}")
         if n == V.shape[0]:
@@ -170,11 +177,12 @@ def max_dim_bound(generators: np.ndarray) -> int:
 def alg4_orthonormalization(generators: np.ndarray, tol: float, eta_abs: float = 1e-12,
                             saturation_exit: bool = False, max_candidates: int | None = None,
                             capacity: int | None = None, resume: Alg4Result | None = None,
-                            max_dim: int | None = None) -> Alg4Result:
+                            max_dim: int | None = None, tol_mode: str = "relative") -> Alg4Result:
     """Algorithm 4: the dimension-only orthonormalisation method.
 
     generators: (k, d, d) complex array, taken in the given order.
-    tol: relative residual tolerance; eta_abs: absolute floor on ||h||.
+    tol: residual tolerance, relative to ||h|| (tol_mode "relative") or
+    absolute ("absolute"); eta_abs: absolute floor on ||h||.
     max_candidates: stop after this many candidate checks (timing samples);
     the returned result then carries the cursor (l, m) and can be resumed.
     max_dim: raise CapacityError rather than grow past this many elements.
@@ -190,7 +198,7 @@ def alg4_orthonormalization(generators: np.ndarray, tol: float, eta_abs: float =
         n = 0
         # generator pass
         for g in generators:
-            n = _test_and_append(n, np.asarray(g, dtype=np.complex128), tol, eta_abs, res)
+            n = _test_and_append(n, np.asarray(g, dtype=np.complex128), tol, eta_abs, res, tol_mode)
             res.t_last_accept = time.perf_counter() - t0
         l, m = 1, 0
     else:
@@ -208,7 +216,7 @@ def alg4_orthonormalization(generators: np.ndarray, tol: float, eta_abs: float =
             break
         h = bracket(res.V[l], res.V[m])
         n_before = n
-        n = _test_and_append(n, h, tol, eta_abs, res)
+        n = _test_and_append(n, h, tol, eta_abs, res, tol_mode)
         if n > n_before:
             res.t_last_accept = time.perf_counter() - t0
         if budget is not None:

@@ -30,9 +30,13 @@ LC_PREC_FP64 = 0
 LC_PREC_MIXED_BF16X3 = 1
 PRECISIONS = {"fp64": LC_PREC_FP64, "mixed": LC_PREC_MIXED_BF16X3}
 
+LC_TOL_RELATIVE = 0
+LC_TOL_ABSOLUTE = 1
+TOL_MODES = {"relative": LC_TOL_RELATIVE, "absolute": LC_TOL_ABSOLUTE}
+
 # every symbol the public headers declare
 EXPORTED = ["lc_default_options", "lc_status_string", "lc_version", "lie_closure", "lie_closure_dev",
-            "lie_closure_batched", "lie_closure_alg2", "lie_closure_alg2_dev", "lie_closure_alg3",
+            "lie_closure_batched", "lie_closure_batched_dev", "lie_closure_alg2", "lie_closure_alg2_dev", "lie_closure_alg3",
             "lie_closure_alg3_dev", "lie_closure_resume",
             "lie_closure_resume_dev", "lie_closure_pauli", "lie_closure_pauli_dev", "lc_split_gemm_f32",
             "lc_split_gemm_f32_noalloc"]
@@ -52,7 +56,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("eta_abs", ctypes.c_double), ("tau_screen", ctypes.c_double),
                 ("block_k", ctypes.c_int), ("block_k_growth", ctypes.c_int), ("saturation_exit", ctypes.c_int), ("spin_cap", ctypes.c_longlong),
                 ("max_candidates", ctypes.c_longlong), ("verbose", ctypes.c_int), ("profile", ctypes.c_int),
-                ("fault_inject", ctypes.c_int)]
+                ("fault_inject", ctypes.c_int), ("tol_mode", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("ortho_check", ctypes.c_int), ("screen_kappa", ctypes.c_double)]
 
 
 class Report(ctypes.Structure):
@@ -65,7 +70,12 @@ class Report(ctypes.Structure):
                 ("tau_screen", ctypes.c_double), ("max_screen_rej_rel_res", ctypes.c_double),
                 ("kernel_launches", ctypes.c_longlong), ("gemm_launches", ctypes.c_longlong),
                 ("gemm_flops", ctypes.c_double), ("t_phase_s", ctypes.c_double * 6),
-                ("precision", ctypes.c_int), ("status", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("status", ctypes.c_int),
+                ("n_gray", ctypes.c_longlong), ("eps_screen", ctypes.c_double),
+                ("min_acc_screen_rel_res", ctypes.c_double), ("ortho_defect", ctypes.c_double),
+                ("ortho_rows", ctypes.c_longlong), ("block_k_used", ctypes.c_int),
+                ("block_k_growth_used", ctypes.c_int), ("gemm_tile_n", ctypes.c_int), ("gemm_tile_k", ctypes.c_int),
+                ("autotuned", ctypes.c_int), ("autotune_trials", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         out = {}
@@ -104,6 +114,8 @@ def lib():
                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Options),
                                           ctypes.POINTER(Report)]
         L.lie_closure_batched.restype = ctypes.c_int
+        L.lie_closure_batched_dev.argtypes = L.lie_closure_batched.argtypes + [c_p]
+        L.lie_closure_batched_dev.restype = ctypes.c_int
         L.lie_closure_alg2.argtypes = L.lie_closure.argtypes
         L.lie_closure_alg2.restype = ctypes.c_int
         L.lie_closure_alg2_dev.argtypes = L.lie_closure_dev.argtypes
@@ -146,6 +158,8 @@ def make_options(precision="mixed", **kw) -> Options:
     o = Options()
     lib().lc_default_options(ctypes.byref(o))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    if isinstance(kw.get("tol_mode"), str):
+        kw["tol_mode"] = TOL_MODES[kw["tol_mode"]]
     for k, v in kw.items():
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k}")
@@ -290,6 +304,39 @@ def lie_closure_batched(generator_sets, tol: float, max_dims=None, return_basis:
     dims_l = [int(x) for x in dims]
     out_b = [bases[i][:dims_l[i]] for i in range(n)] if bases is not None else None
     return dims_l, [int(x) for x in stat], out_b, [r.as_dict() for r in reps]
+
+
+def lie_closure_batched_dev(generator_sets, tol: float, max_dims=None, bases=None, stream=None,
+                            precision="mixed", **opts):
+    """Algorithm 4 on many independent sets held on the device: each element of
+    ``generator_sets`` is a contiguous (k, d, d) complex128 CUDA tensor;
+    ``bases`` (optional) a list of (max_dim, d, d) complex128 CUDA tensors (or
+    None entries).  Returns (dims, statuses, reports)."""
+    import torch
+    n = len(generator_sets)
+    for g in generator_sets:
+        if not (g.is_cuda and g.dtype == torch.complex128 and g.is_contiguous() and g.dim() == 3):
+            raise ValueError("every generator set must be a contiguous (k, d, d) complex128 CUDA tensor")
+    ks = (ctypes.c_int * n)(*[g.shape[0] for g in generator_sets])
+    ds = (ctypes.c_int * n)(*[g.shape[1] for g in generator_sets])
+    caps = [int(max_dims[i]) if max_dims is not None else generator_sets[i].shape[1] ** 2 for i in range(n)]
+    cap_arr = (ctypes.c_longlong * n)(*caps)
+    gptr = (ctypes.c_void_p * n)(*[g.data_ptr() for g in generator_sets])
+    bptr = None
+    if bases is not None:
+        for i, b in enumerate(bases):
+            if b is not None and not (b.is_cuda and b.dtype == torch.complex128 and b.is_contiguous()
+                                      and b.shape[0] >= caps[i] and tuple(b.shape[1:]) == tuple(generator_sets[i].shape[1:])):
+                raise ValueError("bases[i] must be a contiguous (max_dim, d, d) complex128 CUDA tensor")
+        bptr = (ctypes.c_void_p * n)(*[b.data_ptr() if b is not None else None for b in bases])
+    dims = (ctypes.c_longlong * n)()
+    stat = (ctypes.c_int * n)()
+    reps = (Report * n)()
+    o = make_options(precision, **opts)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    lib().lie_closure_batched_dev(n, gptr, ks, ds, float(tol), bptr, cap_arr, dims, stat, ctypes.byref(o), reps,
+                                  ctypes.c_void_p(s.cuda_stream))
+    return [int(x) for x in dims], [int(x) for x in stat], [r.as_dict() for r in reps]
 
 
 @dataclass

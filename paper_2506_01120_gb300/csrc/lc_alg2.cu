@@ -295,7 +295,7 @@ class Closure2 {
     A2_TRY(gemm_nn_sub_f64(kb, P_, N, X_, (int)ncap_, B64_, ldp_, R64_, ldp_, s_));        // R = H - X B
     A2_TRY(rownorm2_f64(kb, P_, R64_, ldp_, rn2_, s_));
     const double tau = 0.5 * tol_;
-    A2_TRY(screen_compact_f64(unit_, rn2_, kb, 0.5, tau * tau, idx_, stats_, s_));
+    A2_TRY(screen_compact_f64(unit_, rn2_, kb, 0.5, tau * tau, 0.0, idx_, stats_, s_));
     A2_TRY(cudaMemcpyAsync(&host_->stats, stats_, sizeof(DevStats), cudaMemcpyDeviceToHost, s_));
     A2_TRY(cudaStreamSynchronize(s_));
     const int f = host_->stats.nflag;

@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -102,7 +103,22 @@ struct HostMirror {
   double maxdev, maxabs;
   int nonfinite;
   int nnz;
+  unsigned long long scratch_bits;
 };
+
+// Autotuner cache: the screening-GEMM tile and saturated-phase block size
+// chosen for (device, d, Algorithm 3 or 4).
+struct TuneKey {
+  int dev, d, alg3;
+  bool operator<(const TuneKey& o) const {
+    return dev != o.dev ? dev < o.dev : (d != o.d ? d < o.d : alg3 < o.alg3);
+  }
+};
+struct TuneVal {
+  int cfg, kb;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
 
 class Closure {
  public:
@@ -114,7 +130,7 @@ class Closure {
     // packed components as its N extent)
     ldp_ = round_up(P_, std::max(128, split_gemm_tile_n()));
     ncap_pad_ = (int)round_up_ll(ncap_, std::max(128, split_gemm_tile_n()));
-    int K = o.block_k > 0 ? o.block_k : (mixed_ ? 16384 : 2048);
+    int K = o.block_k > 0 ? o.block_k : (mixed_ ? (o.autotune ? 32768 : 16384) : 2048);
     // bound the candidate buffers to about 8 GB
     const double per = mixed_ ? (8.0 * ldp_ + 4.0 * ldp_ + 4.0 * ncap_pad_ + 8.0 * ncap_)
                               : (24.0 * ldp_ + 8.0 * ncap_);
@@ -124,7 +140,15 @@ class Closure {
     K_ = std::max(1, K);
     Kpad_ = round_up(K_, 128);
     Kgrow_ = std::min(K_, o.block_k_growth > 0 ? o.block_k_growth : 1024);
-    tau_ = o.tau_screen > 0 ? o.tau_screen : 1e-3;
+    // saturated-phase block: the allocated K_, except that an autotuned call
+    // without an explicit block_k starts from the fixed default
+    Ksat_ = (o.autotune && o.block_k <= 0) ? std::min(K_, mixed_ ? 16384 : 2048) : K_;
+    measured_tau_ = mixed_ && !(o.tau_screen > 0);
+    tau_ = o.tau_screen > 0 ? o.tau_screen : kTauHi;
+    kappa_ = o.screen_kappa > 0 ? o.screen_kappa : 10.0;
+    // accept iff ||r||^2 > a ||h||^2 + b: relative (a, b) = (tol^2, 0), absolute (0, tol^2)
+    tol_rel2_ = o.tol_mode == LC_TOL_ABSOLUTE ? 0.0 : tol * tol;
+    tol_abs2_ = o.tol_mode == LC_TOL_ABSOLUTE ? tol * tol : 0.0;
     eta_ = o.eta_abs > 0 ? o.eta_abs : 1e-12;
     eta_screen_ = std::max(eta_, 1e-5);
     big_bracket_ = mixed_ && !bracket_tc_supported(d) && bracket_big_supported(d);
@@ -148,6 +172,10 @@ class Closure {
     int rc = setup(d_gens);
     if (rc == LC_OK) rc = (n_resume_ >= 0) ? resume_state() : generator_pass();
     if (rc == LC_OK) rc = sweep();
+    if ((rc == LC_OK || rc == LC_ERR_CAPACITY) && opt.ortho_check) {
+      const int rc2 = ortho_check();
+      if (rc2 != LC_OK) rc = rc2;
+    }
     if (rc == LC_OK || rc == LC_ERR_CAPACITY) {
       if (d_basis_out && N_ > 0) {
         cudaError_t e = unpack_basis(V64_, (int)N_, d_, ldp_, d_basis_out, s_);
@@ -182,10 +210,25 @@ class Closure {
       }
       rep->min_acc_rel_res = mn;
       rep->max_rej_rel_res = mx;
-      rep->tau_screen = mixed_ ? tau_ : 0.5 * tol_;
-      double sr = 0.0;
-      if (host_) memcpy(&sr, &host_->stats.max_screen_rej_bits, 8);
+      double sr = 0.0, eps = 0.0, mas = 0.0;
+      if (host_) {
+        memcpy(&sr, &host_->stats.max_screen_rej_bits, 8);
+        memcpy(&eps, &host_->stats.eps_bits, 8);
+        memcpy(&mas, &host_->stats.min_acc_screen_bits, 8);
+      }
+      rep->tau_screen = mixed_ ? (measured_tau_ ? tau_max_used_ : tau_) : 0.5 * tol_;
       rep->max_screen_rej_rel_res = sr;
+      rep->n_gray = gray_;
+      rep->eps_screen = mixed_ ? eps : 0.0;
+      rep->min_acc_screen_rel_res = mixed_ ? mas : 0.0;
+      rep->ortho_defect = ortho_defect_;
+      rep->ortho_rows = ortho_rows_;
+      rep->block_k_used = Ksat_;
+      rep->block_k_growth_used = Kgrow_;
+      rep->gemm_tile_n = split_gemm_tile_n(gemm_cfg_);
+      rep->gemm_tile_k = split_gemm_tile_k(gemm_cfg_);
+      rep->autotuned = autotuned_ ? 1 : 0;
+      rep->autotune_trials = trials_done_;
       rep->kernel_launches = launches_ + 1 + (N_ > 0 && d_basis_out ? 1 : 0);
       rep->gemm_launches = gemm_launches_;
       rep->gemm_flops = gemm_flops_;
@@ -203,8 +246,27 @@ class Closure {
   }
 
  private:
-  int k_, d_, P_, ldp_, ncap_pad_, K_, Kpad_, Kgrow_;
+  int k_, d_, P_, ldp_, ncap_pad_, K_, Kpad_, Kgrow_, Ksat_;
   double tol_, tau_, eta_, eta_screen_;
+  double tol_rel2_ = 0.0, tol_abs2_ = 0.0;
+  // measured screen threshold (mixed mode, opt.tau_screen == 0)
+  static constexpr double kTauHi = 1e-3;                // upper clamp (and the fixed default before any probe)
+  static constexpr double kTauLo = 4.76837158203125e-7; // 2^-21, a few FP32 ulps
+  static constexpr int kProbeRows = 128, kProbeSingles = 64;
+  bool measured_tau_ = false;
+  double kappa_ = 10.0, tau_max_used_ = 0.0;
+  long long N_probe_ = 0, probes_ = 0, gray_ = 0;
+  float* rho2f_ = nullptr;            // screened rho^2 of the flagged candidates, flag order
+  // orthonormality check
+  double* G64_ = nullptr;
+  unsigned long long* defect_bits_ = nullptr;
+  double ortho_defect_ = -1.0;
+  long long ortho_rows_ = 0;
+  static constexpr int kOrthoSample = 4096, kOrthoChunk = 128;
+  // screening GEMM tile and the autotuner
+  int gemm_cfg_ = 0;
+  bool autotuned_ = false;
+  int trials_done_ = 0;
   long long ncap_;
   lc_options opt;
   cudaStream_t s_;
@@ -218,7 +280,7 @@ class Closure {
   long long N_ = 0, t_ = 0, checked_ = 0, nonzero_ = 0, flagged_ = 0, blocks_ = 0;
   double t_last_accept_ = 0.0;
   // device buffers
-  double *G64_ = nullptr, *V64_ = nullptr, *H64_ = nullptr, *S64_ = nullptr, *R64_ = nullptr, *beta64_ = nullptr;
+  double *Gen64_ = nullptr, *V64_ = nullptr, *H64_ = nullptr, *S64_ = nullptr, *R64_ = nullptr, *beta64_ = nullptr;
   double *hn2_ = nullptr, *rn2_ = nullptr, *hnf_ = nullptr, *rnf_ = nullptr, *chk_ = nullptr, *hn2c64_ = nullptr;
   int *idx_ = nullptr, *nonfinite_ = nullptr, *need_ = nullptr;
   unsigned int* bar_ = nullptr;
@@ -234,7 +296,11 @@ class Closure {
   bool tc_bracket_ = false, big_bracket_ = false, q_bracket_ = false;
 
   void carve() {
-    G64_ = ar_.take<double>((size_t)k_ * ldp_);
+    if (opt.ortho_check) {
+      G64_ = ar_.take<double>((size_t)kOrthoChunk * kOrthoSample);
+      defect_bits_ = ar_.take<unsigned long long>(1);
+    }
+    Gen64_ = ar_.take<double>((size_t)k_ * ldp_);
     V64_ = ar_.take<double>((size_t)ncap_ * ldp_);
     R64_ = ar_.take<double>((size_t)K_ * ldp_);
     beta64_ = ar_.take<double>((size_t)K_ * ncap_);
@@ -275,6 +341,7 @@ class Closure {
       Chi_ = ar_.take<__nv_bfloat16>((size_t)Kpad_ * ldp_);
       Clo_ = ar_.take<__nv_bfloat16>((size_t)Kpad_ * ldp_);
       hn2c_ = ar_.take<float>(Kpad_);
+      rho2f_ = ar_.take<float>(Kpad_);
       nz_idx_ = ar_.take<int>(Kpad_);
       nnz_ = ar_.take<int>(1);
       if (tc_bracket_) {
@@ -335,12 +402,15 @@ class Closure {
       memset(&init, 0, sizeof(init));
       double inf = INFINITY;
       memcpy(&init.min_acc_bits, &inf, 8);
+      memcpy(&init.min_acc_screen_bits, &inf, 8);
+      init.tau2 = (float)(tau_ * tau_);
+      init.eps2 = 0.f;
       host_->stats = init;
       LC_TRY(cudaMemcpyAsync(stats_, &host_->stats, sizeof(DevStats), cudaMemcpyHostToDevice, s_));
     }
     LC_TRY(cudaMemsetAsync(chk_, 0, 2 * sizeof(double), s_));
     LC_TRY(cudaMemsetAsync(nonfinite_, 0, sizeof(int), s_));
-    LC_TRY(pack_generators(d_gens, k_, d_, ldp_, G64_, chk_, chk_ + 1, nonfinite_, s_));
+    LC_TRY(pack_generators(d_gens, k_, d_, ldp_, Gen64_, chk_, chk_ + 1, nonfinite_, s_));
     LC_TRY(cudaMemcpyAsync(&host_->maxdev, chk_, 2 * sizeof(double), cudaMemcpyDeviceToHost, s_));
     LC_TRY(cudaMemcpyAsync(&host_->nonfinite, nonfinite_, sizeof(int), cudaMemcpyDeviceToHost, s_));
     LC_TRY(cudaStreamSynchronize(s_));
@@ -349,11 +419,11 @@ class Closure {
     if (opt.saturation_exit) {
       // largest possible dimension: d^2 - 1, plus the trace direction
       std::vector<double> diag((size_t)k_ * d_);
-      LC_TRY(cudaMemcpy2DAsync(diag.data(), sizeof(double), G64_, sizeof(double) * (d_ + 1), sizeof(double),
+      LC_TRY(cudaMemcpy2DAsync(diag.data(), sizeof(double), Gen64_, sizeof(double) * (d_ + 1), sizeof(double),
                                (size_t)d_, cudaMemcpyDeviceToHost, s_));
       // the 2-D copy above walks one generator's diagonal; repeat per generator
       for (int q = 1; q < k_; ++q)
-        LC_TRY(cudaMemcpy2DAsync(diag.data() + (size_t)q * d_, sizeof(double), G64_ + (size_t)q * ldp_,
+        LC_TRY(cudaMemcpy2DAsync(diag.data() + (size_t)q * d_, sizeof(double), Gen64_ + (size_t)q * ldp_,
                                  sizeof(double) * (d_ + 1), sizeof(double), (size_t)d_, cudaMemcpyDeviceToHost,
                                  s_));
       LC_TRY(cudaStreamSynchronize(s_));
@@ -425,7 +495,7 @@ class Closure {
   // classical Gram-Schmidt against the basis as it was when the block
   // started (a second pass only when some row needs it), then the in-order
   // test and append against that basis plus this block's accepts.
-  int accept_rows(int f) {
+  int accept_rows(int f, const float* rho2_screen = nullptr) {
     flagged_ += f;
     ph_begin();
     if (alg3_)   // the raw bracket (or generator) is what Algorithm 3 appends to B
@@ -437,7 +507,7 @@ class Closure {
       LC_TRY(gemm_nt_f64(f, n0, P_, R64_, ldp_, V64_, ldp_, beta64_, (int)ncap_, s_, ws64_, kWs64));
       LC_TRY(gemm_nn_sub_f64(f, P_, n0, beta64_, (int)ncap_, V64_, ldp_, R64_, ldp_, s_, ws64_, kWs64));
       LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, rnf_, s_));
-      LC_TRY(need_pass2(f, hnf_, rnf_, eta_ * eta_, tol_, need_, s_));
+      LC_TRY(need_pass2(f, hnf_, rnf_, eta_ * eta_, tol_rel2_, tol_abs2_, need_, s_));
       LC_TRY(gemm_nt_f64(f, n0, P_, R64_, ldp_, V64_, ldp_, beta64_, (int)ncap_, s_, ws64_, kWs64, need_));
       LC_TRY(gemm_nn_sub_f64(f, P_, n0, beta64_, (int)ncap_, V64_, ldp_, R64_, ldp_, s_, ws64_, kWs64, need_));
       LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, rnf_, s_, need_));
@@ -446,9 +516,9 @@ class Closure {
       LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, rnf_, s_));
     }
     LC_TRY(zero_stats(stats_, n0, s_));
-    LC_TRY(accept_seq(f, R64_, ldp_, rnf_, hnf_, tol_, eta_ * eta_, V64_, ldp_, (int)ncap_, P_, stats_, st_, bar_,
-                      opt.spin_cap, s_, opt.fault_inject ? 1 : 0, alg3_ ? Hraw_ : nullptr, alg3_ ? B64_ : nullptr,
-                      alg3_ ? bn2_ : nullptr));
+    LC_TRY(accept_seq(f, R64_, ldp_, rnf_, hnf_, tol_rel2_, tol_abs2_, eta_ * eta_, V64_, ldp_, (int)ncap_, P_,
+                      stats_, st_, bar_, opt.spin_cap, s_, opt.fault_inject ? 1 : 0, alg3_ ? Hraw_ : nullptr,
+                      alg3_ ? B64_ : nullptr, alg3_ ? bn2_ : nullptr, rho2_screen));
     launches_ += 4;
     ph_end(PH_ACCEPT);
     int rc = sync_read();
@@ -472,7 +542,7 @@ class Closure {
   int resume_state() {
     if (n_resume_ > ncap_) return LC_ERR_CAPACITY;
     // the packed elements are already the basis rows
-    LC_TRY(cudaMemcpy2DAsync(V64_, sizeof(double) * ldp_, G64_, sizeof(double) * ldp_, sizeof(double) * P_,
+    LC_TRY(cudaMemcpy2DAsync(V64_, sizeof(double) * ldp_, Gen64_, sizeof(double) * ldp_, sizeof(double) * P_,
                              (size_t)n_resume_, cudaMemcpyDeviceToDevice, s_));
     if (mixed_ && n_resume_ > 0) {
       LC_TRY(split_rows(V64_, ldp_, 0, (int)n_resume_, P_, Vhi_, Vlo_, ldp_, VThi_, VTlo_, ncap_pad_, s_));
@@ -486,7 +556,7 @@ class Closure {
   }
 
   int generator_pass() {
-    LC_TRY(cudaMemcpy2DAsync(R64_, sizeof(double) * ldp_, G64_, sizeof(double) * ldp_, sizeof(double) * P_, k_,
+    LC_TRY(cudaMemcpy2DAsync(R64_, sizeof(double) * ldp_, Gen64_, sizeof(double) * ldp_, sizeof(double) * P_, k_,
                              cudaMemcpyDeviceToDevice, s_));
     return accept_rows(k_);
   }
@@ -495,7 +565,11 @@ class Closure {
     int rc = sync_read();
     if (rc != LC_OK) return rc;
     nonzero_ += host_->stats.nnonzero;
-    if (mixed_) gemm_flops_ += 2.0 * 6.0 * (double)host_->stats.nnonzero * (double)N_ * (double)P_;
+    if (mixed_) {
+      gemm_flops_ += 2.0 * 6.0 * (double)host_->stats.nnonzero * (double)N_ * (double)P_;
+      gray_ += host_->stats.ngray;
+      if (measured_tau_) tau_max_used_ = std::max(tau_max_used_, std::sqrt((double)host_->stats.tau2));
+    }
     const int f = host_->stats.nflag;
     if (f > 0) {
       if (mixed_) {
@@ -506,7 +580,7 @@ class Closure {
         LC_TRY(gather_rows_f64(H64_, ldp_, idx_, f, P_, R64_, ldp_, s_));
       }
       launches_ += 1;
-      return accept_rows(f);
+      return accept_rows(f, mixed_ ? rho2f_ : nullptr);
     }
     return LC_OK;
   }
@@ -537,37 +611,68 @@ class Closure {
     LC_TRY(gemm_nn_sub_f64(nnz, P_, (int)N_, beta64_, (int)ncap_, V64_, ldp_, S64_, ldp_, s_, ws64_, kWs64));
     LC_TRY(rownorm2_f64(nnz, P_, S64_, ldp_, rn2_, s_));
     ph_end(PH_GEMM2);
-    // one FP64 projection pass: ||r1|| <= tol/2 ||h|| implies the two-pass
-    // residual is below tol ||h|| as well, so such candidates are dependent
-    const double tau = 0.5 * tol_;
+    // one FP64 projection pass: ||r1|| at most half the accept threshold
+    // implies the two-pass residual is below it as well, so such candidates
+    // are dependent
     ph_begin();
-    LC_TRY(screen_compact_f64(hn2c64_, rn2_, nnz, eta_ * eta_, tau * tau, idx_, stats_, s_, nullptr, nz_idx_));
+    LC_TRY(screen_compact_f64(hn2c64_, rn2_, nnz, eta_ * eta_, 0.25 * tol_rel2_, 0.25 * tol_abs2_, idx_, stats_, s_,
+                              nullptr, nz_idx_));
     ph_end(PH_SCREEN);
     launches_ += 4;
     return after_screen(t0);
   }
 
-  int block_mixed(long long t0, int kb) {
+  // Screen noise probe (measured tau_screen): rows in span(V) through the
+  // same split and GEMMs as a block's candidates; their screened residual is
+  // pure noise.  Re-run whenever |V| has grown by 1/8 since the last probe.
+  int maybe_probe() {
+    if (!measured_tau_ || N_ <= 0) return LC_OK;
+    if (N_probe_ > 0 && 8 * N_ < 9 * N_probe_) return LC_OK;
+    N_probe_ = N_;
+    const int S = kProbeRows;
     ph_begin();
-    if (q_bracket_) {
-      LC_TRY(bracket_q64(Ehi_, Elo_, ncap_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, opt.spin_cap, st_, s_));
-    } else if (big_bracket_) {
-      LC_TRY(bracket_big(Ehi_, Elo_, ncap_, d_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, opt.spin_cap, st_, s_));
-    } else if (tc_bracket_) {
-      LC_TRY(bracket_tc(Ehi_, Elo_, ncap_, d_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, opt.spin_cap, st_, s_));
-    } else {
-      LC_TRY(bracket_mixed(src(), d_, ldp_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, s_));
-    }
-    ph_end(PH_BRACKET);
-    // candidates with a (numerically) zero bracket are rejected outright; the
-    // rest are packed into consecutive rows so the GEMMs skip the zeros
-    const float es = (float)eta_screen_, ts = (float)tau_;
-    ph_begin();
-    // (B is not normalised: for Algorithm 3 the floor scales with ||B_l|| ||B_m||)
-    LC_TRY(compact_nonzero(hn2f_, kb, es * es, nz_idx_, nnz_, s_, alg3_ ? bn2_ : nullptr, t0));
-    LC_TRY(gather_candidates(Hhi_, Hlo_, ldp_, hn2f_, nz_idx_, nnz_, kb, ldp_, Chi_, Clo_, hn2c_, s_));
+    LC_TRY(probe_rows(V64_, ldp_, (int)N_, P_, S, kProbeSingles, 0x2506011200000000ull + (unsigned long long)probes_,
+                      Chi_, Clo_, ldp_, hn2c_, nnz_, s_));
     ph_end(PH_SCREEN);
-    const int M = round_up(kb, 128);
+    LC_TRY(screen_gemms(S));
+    gemm_flops_ += 2.0 * 6.0 * (double)S * (double)N_ * (double)P_;
+    ph_begin();
+    LC_TRY(probe_eps(hn2c_, rn2f_, S, stats_, (float)kappa_, (float)kTauLo, (float)kTauHi, s_));
+    ph_end(PH_SCREEN);
+    ++probes_;
+    launches_ += 4;
+    return LC_OK;
+  }
+
+  // max |<v_i, v_j> - delta_ij| in FP64 over every q-th row of V (all rows
+  // when |V| <= kOrthoSample), in chunks of kOrthoChunk Gram rows.
+  int ortho_check() {
+    ortho_defect_ = -1.0;
+    ortho_rows_ = 0;
+    if (N_ <= 0 || !G64_) return LC_OK;
+    const long long q = (N_ + kOrthoSample - 1) / kOrthoSample;
+    const int S = (int)((N_ + q - 1) / q);
+    const int ld = (int)(q * ldp_);
+    LC_TRY(cudaMemsetAsync(defect_bits_, 0, sizeof(unsigned long long), s_));
+    for (int c0 = 0; c0 < S; c0 += kOrthoChunk) {
+      const int rows = std::min(kOrthoChunk, S - c0);
+      LC_TRY(gemm_nt_f64(rows, S, P_, V64_ + (size_t)c0 * ld, ld, V64_, ld, G64_, S, s_, ws64_, kWs64));
+      LC_TRY(defect_max(G64_, rows, S, S, c0, defect_bits_, s_));
+      launches_ += 3;
+    }
+    unsigned long long bits = 0;
+    LC_TRY(cudaMemcpyAsync(&host_->scratch_bits, defect_bits_, sizeof(bits), cudaMemcpyDeviceToHost, s_));
+    LC_TRY(cudaStreamSynchronize(s_));
+    bits = host_->scratch_bits;
+    memcpy(&ortho_defect_, &bits, 8);
+    ortho_rows_ = S;
+    return LC_OK;
+  }
+
+  // projection beta = C V^T (split BF16 out) and residual ||C - beta V||^2 of
+  // the first *nnz_ rows of C (M rows allocated)
+  cudaError_t screen_gemms(int M_rows) {
+    const int M = round_up(M_rows, 128);
     const int Npad = round_up((int)N_, std::max(128, split_gemm_tile_n()));
     SplitGemmArgs g1;
     memset(&g1, 0, sizeof(g1));
@@ -587,8 +692,10 @@ class Closure {
     g1.epilogue = 0;
     g1.spin_cap = opt.spin_cap;
     g1.st = st_;
+    g1.cfg = gemm_cfg_;
     ph_begin();
-    LC_TRY(split_gemm_tcgen05(g1, s_));
+    cudaError_t e = split_gemm_tcgen05(g1, s_);
+    if (e != cudaSuccess) return e;
     ph_end(PH_GEMM1);
     SplitGemmArgs g2;
     memset(&g2, 0, sizeof(g2));
@@ -609,52 +716,171 @@ class Closure {
     g2.epilogue = 1;
     g2.spin_cap = opt.spin_cap;
     g2.st = st_;
-    LC_TRY(cudaMemsetAsync(rn2f_, 0, sizeof(float) * M, s_));
+    g2.cfg = gemm_cfg_;
+    e = cudaMemsetAsync(rn2f_, 0, sizeof(float) * M, s_);
+    if (e != cudaSuccess) return e;
     ph_begin();
-    LC_TRY(split_gemm_tcgen05(g2, s_));
+    e = split_gemm_tcgen05(g2, s_);
+    if (e != cudaSuccess) return e;
     ph_end(PH_GEMM2);
     gemm_launches_ += 2;
+    return cudaSuccess;
+  }
+
+  int block_mixed(long long t0, int kb) {
+    {
+      const int rc = maybe_probe();
+      if (rc != LC_OK) return rc;
+    }
     ph_begin();
-    LC_TRY(screen_compact_f32(hn2c_, rn2f_, kb, es * es, ts * ts, idx_, stats_, s_, nnz_, nz_idx_));
+    if (q_bracket_) {
+      LC_TRY(bracket_q64(Ehi_, Elo_, ncap_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, opt.spin_cap, st_, s_));
+    } else if (big_bracket_) {
+      LC_TRY(bracket_big(Ehi_, Elo_, ncap_, d_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, opt.spin_cap, st_, s_));
+    } else if (tc_bracket_) {
+      LC_TRY(bracket_tc(Ehi_, Elo_, ncap_, d_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, opt.spin_cap, st_, s_));
+    } else {
+      LC_TRY(bracket_mixed(src(), d_, ldp_, t0, kb, Hhi_, Hlo_, ldp_, hn2f_, s_));
+    }
+    ph_end(PH_BRACKET);
+    // candidates with a (numerically) zero bracket are rejected outright; the
+    // rest are packed into consecutive rows so the GEMMs skip the zeros
+    const float es = (float)eta_screen_, ts = (float)tau_;
+    ph_begin();
+    // (B is not normalised: for Algorithm 3 the floor scales with ||B_l|| ||B_m||)
+    LC_TRY(compact_nonzero(hn2f_, kb, es * es, nz_idx_, nnz_, s_, alg3_ ? bn2_ : nullptr, t0));
+    LC_TRY(gather_candidates(Hhi_, Hlo_, ldp_, hn2f_, nz_idx_, nnz_, kb, ldp_, Chi_, Clo_, hn2c_, s_));
+    ph_end(PH_SCREEN);
+    LC_TRY(screen_gemms(kb));
+    ph_begin();
+    LC_TRY(screen_compact_f32(hn2c_, rn2f_, kb, es * es, ts * ts, idx_, stats_, s_, nnz_, nz_idx_,
+                              measured_tau_ ? 1 : 0, rho2f_));
     ph_end(PH_SCREEN);
     launches_ += 6;
     return after_screen(t0);
   }
 
   // Block sizes: Kgrow_ while the basis grows (bounds the in-block sequential
-  // work and the duplicates screened in together), doubling up to K_ once a
+  // work and the duplicates screened in together), doubling up to Ksat_ once a
   // block appends nothing.  Any partition of the pair order gives the same
   // result.
+  //
+  // Autotuner (mixed mode, opt.autotune): the blocks that follow a block that
+  // appended nothing are trials -- each screening-GEMM tile configuration with
+  // each block size in kTrialK (up to the allocated K_) -- timed with CUDA
+  // events from the bracket launch to the end of the block.  The fastest
+  // (candidates per second) is kept for the rest of the call and cached per
+  // (device, d, algorithm); a cached choice is used without trials.  A trial
+  // that was cut short or appended something is repeated on the next
+  // saturated block.
+  static constexpr int kTrialK[4] = {4096, 8192, 16384, 32768};
+  struct Trial { int cfg, kb; double rate; };
+  std::vector<Trial> trials_;
+  size_t trial_next_ = 0;
+  bool tuning_ = false;
+
+  void autotune_setup() {
+    if (!opt.autotune || !mixed_) return;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+      std::lock_guard<std::mutex> g(g_tune_mu);
+      auto it = g_tune.find(TuneKey{dev, d_, alg3_ ? 1 : 0});
+      if (it != g_tune.end()) {
+        gemm_cfg_ = it->second.cfg;
+        Ksat_ = std::min(K_, it->second.kb);
+        autotuned_ = true;
+        return;
+      }
+    }
+    for (int c = 0; c < split_gemm_num_cfgs(); ++c)
+      for (int kb : kTrialK)
+        if (kb <= K_) trials_.push_back({c, kb, 0.0});
+    if (trials_.empty()) trials_.push_back({0, K_, 0.0});
+    tuning_ = true;
+  }
+
+  void autotune_finish() {
+    tuning_ = false;
+    const Trial* best = &trials_[0];
+    for (const Trial& t : trials_)
+      if (t.rate > best->rate) best = &t;
+    gemm_cfg_ = best->cfg;
+    Ksat_ = best->kb;
+    autotuned_ = true;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[TuneKey{dev, d_, alg3_ ? 1 : 0}] = TuneVal{best->cfg, best->kb};
+  }
+
   int sweep() {
     t_ = n_resume_ >= 0 ? t_resume_ : 0;
+    autotune_setup();
     long long knext = Kgrow_;
+    bool saturated = false;              // the previous block appended nothing
+    cudaEvent_t ta = nullptr, tb = nullptr;
+    if (tuning_) {
+      cudaEventCreate(&ta);
+      cudaEventCreate(&tb);
+    }
+    int rc = LC_OK;
     for (;;) {
       const long long T = pairs_below(N_);
       if (t_ >= T) break;
       if (dmax_ >= 0 && N_ >= dmax_) break;
-      long long kb = std::min<long long>(std::min<long long>(knext, K_), T - t_);
+      const bool trial = tuning_ && saturated && trial_next_ < trials_.size();
+      long long want = trial ? trials_[trial_next_].kb : std::min<long long>(knext, Ksat_);
+      if (trial) gemm_cfg_ = trials_[trial_next_].cfg;
+      long long kb = std::min<long long>(want, T - t_);
       if (opt.max_candidates > 0) kb = std::min<long long>(kb, opt.max_candidates - checked_);
       if (kb <= 0) break;
       const long long n_before = N_;
-      int rc = mixed_ ? block_mixed(t_, (int)kb) : block_fp64(t_, (int)kb);
-      knext = (N_ > n_before) ? Kgrow_ : std::min<long long>(2 * kb, K_);
+      if (trial) cudaEventRecord(ta, s_);
+      rc = mixed_ ? block_mixed(t_, (int)kb) : block_fp64(t_, (int)kb);
+      if (trial && rc == LC_OK) {
+        cudaEventRecord(tb, s_);
+        float ms = 0.f;
+        if (cudaEventSynchronize(tb) == cudaSuccess && cudaEventElapsedTime(&ms, ta, tb) == cudaSuccess &&
+            kb == want && N_ == n_before && ms > 0.f) {
+          trials_[trial_next_].rate = (double)kb / (1e-3 * ms);
+          ++trial_next_;
+          ++trials_done_;
+          if (trial_next_ == trials_.size()) autotune_finish();
+        }
+      }
+      saturated = (N_ == n_before);
+      knext = saturated ? std::min<long long>(2 * kb, Ksat_) : Kgrow_;
       ++blocks_;
       t_ += kb;
       checked_ += kb;
       if (opt.verbose)
-        fprintf(stderr, "lieclosure: block %lld t=%lld kb=%lld flagged=%d dim %lld -> %lld\n", blocks_, t_ - kb, kb,
-                host_ ? host_->stats.nflag : -1, n_before, N_);
-      if (rc != LC_OK) return rc;
+        fprintf(stderr, "lieclosure: block %lld t=%lld kb=%lld cfg=%d flagged=%d dim %lld -> %lld\n", blocks_, t_ - kb,
+                kb, gemm_cfg_, host_ ? host_->stats.nflag : -1, n_before, N_);
+      if (rc != LC_OK) break;
     }
-    return LC_OK;
+    if (tuning_) {
+      // trials left unfinished: keep the best measured so far for this call
+      // (not cached), else the defaults
+      const Trial* best = nullptr;
+      for (const Trial& t : trials_)
+        if (t.rate > 0 && (!best || t.rate > best->rate)) best = &t;
+      gemm_cfg_ = best ? best->cfg : 0;
+      tuning_ = false;
+    }
+    if (ta) cudaEventDestroy(ta);
+    if (tb) cudaEventDestroy(tb);
+    return rc;
   }
 };
 
 int check_args(const void* g, int k, int d, double tol, long long max_dim, const lc_options& o) {
   if (!g || k < 1 || d < 2 || !(tol > 0.0) || max_dim < 1) return LC_ERR_ARG;
   if (o.precision != LC_PREC_FP64 && o.precision != LC_PREC_MIXED_BF16X3) return LC_ERR_ARG;
-  if (o.block_k < 0 || o.block_k_growth < 0 || o.tau_screen < 0 || o.eta_abs < 0 || o.max_candidates < 0)
+  if (o.block_k < 0 || o.block_k_growth < 0 || o.tau_screen < 0 || o.eta_abs < 0 || o.max_candidates < 0 ||
+      o.screen_kappa < 0 || !(o.screen_kappa == o.screen_kappa))
     return LC_ERR_ARG;
+  if (o.tol_mode != LC_TOL_RELATIVE && o.tol_mode != LC_TOL_ABSOLUTE) return LC_ERR_ARG;
   if ((long long)d * d > (1ll << 31) / 2) return LC_ERR_ARG;
   return LC_OK;
 }
@@ -713,9 +939,12 @@ int closure_host(const lc_c128* generators, int k, int d, double tol, lc_c128* b
 // Independent sets: worker threads, one CUDA stream each, take sets in order
 // of decreasing size (d, then k) from a shared cursor, so the long closures
 // start first and the many small, latency-bound ones fill the gaps.
+// With parent != nullptr (the device-pointer form) the worker streams first
+// wait for the work queued on parent, and each set runs closure_device on its
+// device buffers.
 int batched_host(int nsets, const lc_c128* const* generators, const int* k, const int* d, double tol,
                  lc_c128* const* basis_out, const long long* max_dim, long long* dim_out, int* status_out,
-                 const lc_options& o, lc_report* rep) {
+                 const lc_options& o, lc_report* rep, bool device = false, cudaStream_t parent = nullptr) {
   std::vector<int> order(nsets);
   for (int i = 0; i < nsets; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
@@ -727,18 +956,36 @@ int batched_host(int nsets, const lc_c128* const* generators, const int* k, cons
   const int nworkers = std::max(1, std::min(nsets, 16));
   std::atomic<int> next(0);
   std::vector<int> status(nsets, LC_OK);
+  cudaEvent_t ready = nullptr;
+  if (device) {
+    if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) return LC_ERR_CUDA;
+    if (cudaEventRecord(ready, parent) != cudaSuccess) {
+      cudaEventDestroy(ready);
+      return LC_ERR_CUDA;
+    }
+  }
   auto work = [&]() {
     cudaSetDevice(dev);
     cudaStream_t s;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+        (device && cudaStreamWaitEvent(s, ready, 0) != cudaSuccess)) {
       for (int i = next.fetch_add(1); i < nsets; i = next.fetch_add(1)) status[order[i]] = LC_ERR_CUDA;
       return;
     }
     for (int i = next.fetch_add(1); i < nsets; i = next.fetch_add(1)) {
       const int q = order[i];
       long long dim = 0;
-      status[q] = closure_host(generators[q], k[q], d[q], tol, basis_out ? basis_out[q] : nullptr, &dim,
-                               max_dim[q], o, rep ? rep + q : nullptr, s);
+      lc_c128* out = basis_out ? basis_out[q] : nullptr;
+      if (device) {
+        status[q] = check_args(generators[q], k[q], d[q], tol, max_dim[q], o);
+        if (status[q] == LC_OK)
+          status[q] = closure_device(reinterpret_cast<const double2*>(generators[q]), k[q], d[q], tol,
+                                     reinterpret_cast<double2*>(out), &dim, max_dim[q], o, rep ? rep + q : nullptr,
+                                     s);
+      } else {
+        status[q] = closure_host(generators[q], k[q], d[q], tol, out, &dim, max_dim[q], o, rep ? rep + q : nullptr,
+                                 s);
+      }
       if (dim_out) dim_out[q] = dim;
     }
     cudaStreamDestroy(s);
@@ -746,6 +993,7 @@ int batched_host(int nsets, const lc_c128* const* generators, const int* k, cons
   std::vector<std::thread> pool;
   for (int w = 0; w < nworkers; ++w) pool.emplace_back(work);
   for (auto& t : pool) t.join();
+  if (ready) cudaEventDestroy(ready);
   int first = LC_OK;
   for (int q = 0; q < nsets; ++q) {
     if (status_out) status_out[q] = status[q];
@@ -763,7 +1011,11 @@ void lc_default_options(lc_options* o) {
   memset(o, 0, sizeof(*o));
   o->precision = LC_PREC_MIXED_BF16X3;
   o->eta_abs = 1e-12;
-  o->tau_screen = 1e-3;
+  o->tau_screen = 0.0;          // measured
+  o->screen_kappa = 10.0;
+  o->tol_mode = LC_TOL_RELATIVE;
+  o->autotune = 0;
+  o->ortho_check = 0;
   o->block_k = 0;
   o->saturation_exit = 0;
   o->spin_cap = 0;
@@ -939,6 +1191,17 @@ int lie_closure_batched(int nsets, const lc_c128* const* generators, const int* 
   lc_options o;
   if (opt) o = *opt; else lc_default_options(&o);
   return batched_host(nsets, generators, k, d, tol, basis_out, max_dim, dim_out, status_out, o, rep);
+}
+
+int lie_closure_batched_dev(int nsets, const lc_c128* const* generators, const int* k, const int* d, double tol,
+                            lc_c128* const* basis_out, const long long* max_dim, long long* dim_out, int* status_out,
+                            const lc_options* opt, lc_report* rep, void* stream) {
+  if (nsets < 0 || (nsets > 0 && (!generators || !k || !d || !max_dim))) return LC_ERR_ARG;
+  if (nsets == 0) return LC_OK;
+  lc_options o;
+  if (opt) o = *opt; else lc_default_options(&o);
+  return batched_host(nsets, generators, k, d, tol, basis_out, max_dim, dim_out, status_out, o, rep, true,
+                      static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -281,14 +281,19 @@ __global__ void k_gather_rows(const double* __restrict__ src, int lds, const int
 // Ordered compaction of the flagged candidates (one CTA of 1024 threads).
 template <typename T>
 __global__ void __launch_bounds__(1024) k_screen_compact(const T* __restrict__ hn2, const T* __restrict__ rn2,
-                                                         int count, T eta2, T tau2, int* __restrict__ idx,
+                                                         int count, T eta2, T tau2, T tau2_abs, int* __restrict__ idx,
                                                          DevStats* stats, const int* __restrict__ count_dev,
-                                                         const int* __restrict__ map) {
+                                                         const int* __restrict__ map, int measured,
+                                                         float* __restrict__ rho2_flag) {
   if (count_dev) count = min(count, *count_dev);
+  // measured threshold: tau^2 and the probe's eps^2 live in the stats block
+  if (measured) tau2 = (T)stats->tau2;
+  const double eps2 = measured ? (double)stats->eps2 : -1.0;
+  int gray = 0;
   __shared__ int wsum[32];
-  __shared__ int base, nz_total;
+  __shared__ int base, nz_total, gray_total;
   __shared__ double wmax[32];
-  if (threadIdx.x == 0) { base = 0; nz_total = 0; }
+  if (threadIdx.x == 0) { base = 0; nz_total = 0; gray_total = 0; }
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   double rej_max = 0.0;
@@ -298,10 +303,13 @@ __global__ void __launch_bounds__(1024) k_screen_compact(const T* __restrict__ h
     int f = 0;
     if (c < count) {
       const T h = hn2[c], r = rn2[c];
-      f = (h > eta2 && r > tau2 * h) ? 1 : 0;
+      f = (h > eta2 && r > tau2 * h + tau2_abs) ? 1 : 0;
       if (h > eta2) {
         ++nz;
-        if (!f) rej_max = fmax(rej_max, sqrt((double)r / (double)h));
+        if (!f) {
+          rej_max = fmax(rej_max, sqrt((double)r / (double)h));
+          if ((double)r > eps2 * (double)h && eps2 >= 0.0) ++gray;
+        }
       }
     }
     const unsigned mask = __ballot_sync(0xffffffffu, f);
@@ -318,7 +326,10 @@ __global__ void __launch_bounds__(1024) k_screen_compact(const T* __restrict__ h
     }
     __syncthreads();
     const int off = base + (w ? wsum[w - 1] : 0) + pre;
-    if (f) idx[off] = map ? map[c] : c;
+    if (f) {
+      idx[off] = map ? map[c] : c;
+      if (rho2_flag) rho2_flag[off] = (float)((double)rn2[c] / (double)hn2[c]);
+    }
     __syncthreads();
     if (threadIdx.x == 0) base += wsum[31];
     __syncthreads();
@@ -326,10 +337,12 @@ __global__ void __launch_bounds__(1024) k_screen_compact(const T* __restrict__ h
   for (int o = 16; o > 0; o >>= 1) {
     rej_max = fmax(rej_max, __shfl_xor_sync(0xffffffffu, rej_max, o));
     nz += __shfl_xor_sync(0xffffffffu, nz, o);
+    gray += __shfl_xor_sync(0xffffffffu, gray, o);
   }
   if (lane == 0) {
     wmax[w] = rej_max;
     atomicAdd(&nz_total, nz);
+    if (gray) atomicAdd(&gray_total, gray);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -338,68 +351,8 @@ __global__ void __launch_bounds__(1024) k_screen_compact(const T* __restrict__ h
     atomicMax(&stats->max_screen_rej_bits, dbits(m));
     stats->nflag = base;
     stats->nnonzero = nz_total;
+    stats->ngray = gray_total;
   }
-}
-
-// One step of the sequential in-block accept (Algorithm 4's test and append
-// for flagged candidate i, in pair order).  Rows R[0..f) hold the flagged
-// candidates, already orthogonalised twice against the basis rows that
-// existed when the block started; rn2/hn2 hold their squared residual and
-// bracket norms.  Every CTA takes the same decision
-//   accept  <=>  ||h|| > eta_abs  and  ||r_i|| > tol ||h||.
-// On accept CTA 0 appends w = r_i / ||r_i|| to V, and CTA b >= 1 removes the
-// w component from row i + b twice (so later candidates are tested against
-// the union of the old basis and this block's accepts, as the sequential
-// algorithm does) and refreshes its squared norm.
-__global__ void __launch_bounds__(256) k_accept_step(int i, int f, double* __restrict__ R, int ldr,
-                                                     double* __restrict__ rn2, const double* __restrict__ hn2,
-                                                     double tol, double eta2, double* __restrict__ V, int ldv,
-                                                     int ncap, int P, DevStats* stats, DevStatus* st) {
-  __shared__ double red[33];
-  __shared__ int slot;
-  const double h2 = hn2[i], r2 = rn2[i];
-  const bool nonzero = h2 > eta2;
-  const bool accept = nonzero && (r2 > tol * tol * h2);
-  if (!accept) {
-    if (blockIdx.x == 0 && threadIdx.x == 0 && nonzero)
-      atomicMax(&stats->max_rej_bits, dbits(sqrt(r2 / h2)));
-    return;
-  }
-  const double inv = 1.0 / sqrt(r2);
-  const double* ri = R + (long long)i * ldr;
-  if (blockIdx.x == 0) {
-    if (threadIdx.x == 0) {
-      int s = stats->ncur;
-      if (s >= ncap) {
-        if (atomicCAS(&st->code, 0, (int)LC_ERR_CAPACITY) == 0) { st->where = SITE_ACCEPT_CAPACITY; st->info = i; }
-        s = -1;
-      } else {
-        stats->ncur = s + 1;
-        stats->naccepted += 1;
-        atomicMin(&stats->min_acc_bits, dbits(sqrt(r2 / h2)));
-      }
-      slot = s;
-    }
-    __syncthreads();
-    if (slot >= 0) {
-      double* v = V + (long long)slot * ldv;
-      for (int p = threadIdx.x; p < P; p += blockDim.x) v[p] = ri[p] * inv;
-    }
-    return;
-  }
-  const int j = i + blockIdx.x;
-  if (j >= f) return;
-  double* rj = R + (long long)j * ldr;
-  for (int pass = 0; pass < 2; ++pass) {
-    double s = 0.0;
-    for (int p = threadIdx.x; p < P; p += blockDim.x) s = fma(ri[p], rj[p], s);
-    const double c = block_sum(s, red) * inv * inv;    // <w, r_j> w = (r_i . r_j / ||r_i||^2) r_i
-    for (int p = threadIdx.x; p < P; p += blockDim.x) rj[p] = fma(-c, ri[p], rj[p]);
-  }
-  double s = 0.0;
-  for (int p = threadIdx.x; p < P; p += blockDim.x) s = fma(rj[p], rj[p], s);
-  s = block_sum(s, red);
-  if (threadIdx.x == 0) rn2[j] = s;
 }
 
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The
@@ -451,11 +404,12 @@ __device__ bool grid_barrier(unsigned int* count, unsigned int* gen, unsigned in
 // the updated rows.  A rejected candidate changes nothing, so no barrier.
 __global__ void __launch_bounds__(256) k_accept_seq(int f, double* __restrict__ R, int ldr,
                                                     double* __restrict__ rn2, const double* __restrict__ hn2,
-                                                    double tol, double eta2, double* __restrict__ V, int ldv,
+                                                    double tol_rel2, double tol_abs2, double eta2,
+                                                    double* __restrict__ V, int ldv,
                                                     int ncap, int P, DevStats* stats, DevStatus* st,
                                                     unsigned int* bar, uint64_t limit_ns, int phantom,
                                                     const double* __restrict__ Hraw, double* __restrict__ Bk,
-                                                    double* __restrict__ bn2) {
+                                                    double* __restrict__ bn2, const float* __restrict__ rho2_screen) {
   __shared__ double red[33];
   __shared__ int slot, ok_smem;
   const unsigned int G = gridDim.x;
@@ -463,7 +417,7 @@ __global__ void __launch_bounds__(256) k_accept_seq(int f, double* __restrict__ 
     const double h2 = hn2[i];
     const double r2 = __ldcg(&rn2[i]);
     const bool nonzero = h2 > eta2;
-    if (!(nonzero && r2 > tol * tol * h2)) {
+    if (!(nonzero && r2 > tol_rel2 * h2 + tol_abs2)) {
       if (blockIdx.x == 0 && threadIdx.x == 0 && nonzero) atomicMax(&stats->max_rej_bits, dbits(sqrt(r2 / h2)));
       continue;
     }
@@ -479,6 +433,7 @@ __global__ void __launch_bounds__(256) k_accept_seq(int f, double* __restrict__ 
           stats->ncur = sl + 1;
           stats->naccepted += 1;
           atomicMin(&stats->min_acc_bits, dbits(sqrt(r2 / h2)));
+          if (rho2_screen) atomicMin(&stats->min_acc_screen_bits, dbits(sqrt((double)rho2_screen[i])));
         }
         slot = sl;
       }
@@ -518,11 +473,11 @@ __global__ void __launch_bounds__(256) k_accept_seq(int f, double* __restrict__ 
 // one pass is already accurate to rounding (Daniel, Gragg, Kaufman and
 // Stewart's criterion).  Writes 1 to *need if any row needs the second pass.
 __global__ void k_need_pass2(int f, const double* __restrict__ hn2, const double* __restrict__ rn2, double eta2,
-                             double tol, int* need) {
+                             double tol_rel2, double tol_abs2, int* need) {
   int any = 0;
   for (int i = threadIdx.x; i < f; i += blockDim.x) {
     const double h2 = hn2[i], r2 = rn2[i];
-    if (h2 > eta2 && r2 < 0.5 * h2 && r2 > 0.25 * tol * tol * h2) any = 1;
+    if (h2 > eta2 && r2 < 0.5 * h2 && r2 > 0.25 * (tol_rel2 * h2 + tol_abs2)) any = 1;
   }
   any = __syncthreads_or(any);
   if (threadIdx.x == 0) *need = any;
@@ -566,10 +521,26 @@ __global__ void __launch_bounds__(1024) k_compact_nonzero_f64(const double* __re
   if (threadIdx.x == 0) *nnz = base;
 }
 
+// orthonormality defect of a block of Gram rows: max |G[i][j] - delta|
+__global__ void k_defect_max(const double* __restrict__ G, int rows, int cols, int ldg, int r0,
+                             unsigned long long* out_bits) {
+  double m = 0.0;
+  const long long tot = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / cols), j = (int)(e % cols);
+    const double g = G[(long long)i * ldg + j] - (r0 + i == j ? 1.0 : 0.0);
+    m = fmax(m, fabs(g));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out_bits, dbits(m));
+}
+
 __global__ void k_zero_stats(DevStats* stats, int ncur) {
   stats->ncur = ncur;
   stats->naccepted = 0;
   stats->nflag = 0;
+  stats->ngray = 0;
 }
 
 inline int grid_for(long long n, int block, int cap = 152 * 16) {
@@ -677,28 +648,26 @@ cudaError_t gather_rows_f64(const double* src, int lds, const int* idx, int coun
   return cudaGetLastError();
 }
 
-cudaError_t screen_compact_f64(const double* hn2, const double* rn2, int count, double eta2, double tau2, int* idx,
-                               DevStats* stats, cudaStream_t s, const int* count_dev, const int* map) {
-  k_screen_compact<double><<<1, 1024, 0, s>>>(hn2, rn2, count, eta2, tau2, idx, stats, count_dev, map);
+cudaError_t screen_compact_f64(const double* hn2, const double* rn2, int count, double eta2, double tau2,
+                               double tau2_abs, int* idx, DevStats* stats, cudaStream_t s, const int* count_dev,
+                               const int* map) {
+  k_screen_compact<double><<<1, 1024, 0, s>>>(hn2, rn2, count, eta2, tau2, tau2_abs, idx, stats, count_dev, map, 0,
+                                              nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t screen_compact_f32(const float* hn2, const float* rn2, int count, float eta2, float tau2, int* idx,
-                               DevStats* stats, cudaStream_t s, const int* count_dev, const int* map) {
-  k_screen_compact<float><<<1, 1024, 0, s>>>(hn2, rn2, count, eta2, tau2, idx, stats, count_dev, map);
+                               DevStats* stats, cudaStream_t s, const int* count_dev, const int* map, int measured,
+                               float* rho2_flag) {
+  k_screen_compact<float><<<1, 1024, 0, s>>>(hn2, rn2, count, eta2, tau2, 0.f, idx, stats, count_dev, map,
+                                             measured, rho2_flag);
   return cudaGetLastError();
 }
 
-cudaError_t accept_step(int i, int f, double* R, int ldr, double* rn2, const double* hn2, double tol, double eta2,
-                        double* V, int ldv, int ncap, int P, DevStats* stats, DevStatus* st, int* /*accepted_rows*/,
-                        cudaStream_t s) {
-  k_accept_step<<<f - i, 256, 0, s>>>(i, f, R, ldr, rn2, hn2, tol, eta2, V, ldv, ncap, P, stats, st);
-  return cudaGetLastError();
-}
-
-cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2, double tol, double eta2, double* V,
-                       int ldv, int ncap, int P, DevStats* stats, DevStatus* st, unsigned int* bar, long long spin_cap,
-                       cudaStream_t s, int phantom, const double* Hraw, double* Bk, double* bn2) {
+cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2, double tol_rel2, double tol_abs2,
+                       double eta2, double* V, int ldv, int ncap, int P, DevStats* stats, DevStatus* st,
+                       unsigned int* bar, long long spin_cap, cudaStream_t s, int phantom, const double* Hraw,
+                       double* Bk, double* bn2, const float* rho2_screen) {
   if (f <= 0) return cudaSuccess;
   // co-resident CTAs of the cooperative launch, per device
   static std::mutex mu;
@@ -718,20 +687,28 @@ cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2
   }
   const int G = std::max(1, std::min(nblocks, f));
   uint64_t lim = spin_cap > 0 ? (uint64_t)spin_cap : 4000000000ull;
-  void* args[] = {&f,   &R,     &ldr,   &rn2, (void*)&hn2, &tol,    &eta2,          &V,  &ldv, &ncap, &P,
-                  &stats, &st, &bar, &lim, &phantom,    (void*)&Hraw, &Bk, &bn2};
+  void* args[] = {&f,     &R,   &ldr, &rn2, (void*)&hn2, &tol_rel2,    &tol_abs2, &eta2, &V,   &ldv,
+                  &ncap,  &P,   &stats, &st, &bar,       &lim,         &phantom,  (void*)&Hraw, &Bk, &bn2,
+                  (void*)&rho2_screen};
   return cudaLaunchCooperativeKernel((const void*)k_accept_seq, dim3(G), dim3(256), args, 0, s);
 }
 
-cudaError_t need_pass2(int f, const double* hn2, const double* rn2, double eta2, double tol, int* need,
-                       cudaStream_t s) {
-  k_need_pass2<<<1, 256, 0, s>>>(f, hn2, rn2, eta2, tol, need);
+cudaError_t need_pass2(int f, const double* hn2, const double* rn2, double eta2, double tol_rel2, double tol_abs2,
+                       int* need, cudaStream_t s) {
+  k_need_pass2<<<1, 256, 0, s>>>(f, hn2, rn2, eta2, tol_rel2, tol_abs2, need);
   return cudaGetLastError();
 }
 
 cudaError_t compact_nonzero_f64(const double* hn2, int count, double eta2, int* nz_idx, int* nnz, double* hn2c,
                                 cudaStream_t s) {
   k_compact_nonzero_f64<<<1, 1024, 0, s>>>(hn2, count, eta2, nz_idx, nnz, hn2c);
+  return cudaGetLastError();
+}
+
+cudaError_t defect_max(const double* G, int rows, int cols, int ldg, int r0, unsigned long long* out_bits,
+                       cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  k_defect_max<<<grid_for((long long)rows * cols, 256), 256, 0, s>>>(G, rows, cols, ldg, r0, out_bits);
   return cudaGetLastError();
 }
 

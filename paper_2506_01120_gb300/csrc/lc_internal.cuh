@@ -47,10 +47,16 @@ struct DevStats {
   unsigned long long min_acc_bits;
   unsigned long long max_rej_bits;
   unsigned long long max_screen_rej_bits;  // largest screened rel. residual among screen rejects
+  unsigned long long eps_bits;             // largest probe residual of the run (screen noise floor)
+  unsigned long long min_acc_screen_bits;  // smallest screened rel. residual among accepts
   int ncur;            // current |V| (rows of the FP64 basis)
   int naccepted;       // accepts in the current block
   int nflag;           // flagged candidates in the current block
   int nnonzero;        // candidates above the norm floor in the current block
+  int ngray;           // screen rejects in (eps, tau] in the current block
+  float tau2;          // measured screen threshold tau^2 (mixed mode)
+  float eps2;          // latest probe's eps^2
+  int pad_;
 };
 
 // pair index t = l(l-1)/2 + m, 0 <= m < l  <->  (l, m)
@@ -121,32 +127,35 @@ cudaError_t gemm_nn_sub_f64(int M, int N, int K, const double* A, int lda, const
 cudaError_t rownorm2_f64(int M, int N, const double* A, int lda, double* out, cudaStream_t s,
                          const int* run_if = nullptr);
 // the in-block sequential test-and-append of f flagged rows, one cooperative
-// launch (bar: two zeroed unsigned ints)
-cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2, double tol, double eta2,
-                       double* V, int ldv, int ncap, int P, DevStats* stats, DevStatus* st,
+// launch (bar: two zeroed unsigned ints).  Accept iff hn2 > eta2 and
+// rn2 > tol_rel2 * hn2 + tol_abs2 (relative or absolute tolerance);
+// rho2_screen (optional): the rows' screened relative residuals squared
+cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2, double tol_rel2, double tol_abs2,
+                       double eta2, double* V, int ldv, int ncap, int P, DevStats* stats, DevStatus* st,
                        unsigned int* bar, long long spin_cap, cudaStream_t s, int phantom = 0,
-                       const double* Hraw = nullptr, double* Bk = nullptr, double* bn2 = nullptr);
+                       const double* Hraw = nullptr, double* Bk = nullptr, double* bn2 = nullptr,
+                       const float* rho2_screen = nullptr);
 // *need = 1 iff some row needs a second Gram-Schmidt pass
-cudaError_t need_pass2(int f, const double* hn2, const double* rn2, double eta2, double tol, int* need,
-                       cudaStream_t s);
+cudaError_t need_pass2(int f, const double* hn2, const double* rn2, double eta2, double tol_rel2, double tol_abs2,
+                       int* need, cudaStream_t s);
 cudaError_t gather_rows_f64(const double* src, int lds, const int* idx, int count, int ncols,
                             double* dst, int ldd, cudaStream_t s);
-// flags candidates with hn2 > eta^2 and rn2 > tau^2 hn2; writes the flagged
-// candidate positions in order to idx and their count to stats->nflag
+// flags candidates with hn2 > eta^2 and rn2 > tau^2 hn2 + tau2_abs; writes the
+// flagged candidate positions in order to idx and their count to stats->nflag
 cudaError_t screen_compact_f64(const double* hn2, const double* rn2, int count, double eta2,
-                               double tau2, int* idx, DevStats* stats, cudaStream_t s,
+                               double tau2, double tau2_abs, int* idx, DevStats* stats, cudaStream_t s,
                                const int* count_dev = nullptr, const int* map = nullptr);
 // ordered indices of the candidates with hn2 > eta2, their count (*nnz) and norms
 cudaError_t compact_nonzero_f64(const double* hn2, int count, double eta2, int* nz_idx, int* nnz,
                                 double* hn2c, cudaStream_t s);
-// count_dev (optional): live count on the device; map (optional): idx[i] = map[position]
+// count_dev (optional): live count on the device; map (optional): idx[i] = map[position];
+// measured != 0: tau^2 is stats->tau2 (the probe's threshold) and screen rejects
+// with rho^2 > stats->eps2 are counted in stats->ngray; rho2_flag (optional)
+// receives the flagged candidates' rn2 / hn2 in flag order
 cudaError_t screen_compact_f32(const float* hn2, const float* rn2, int count, float eta2,
                                float tau2, int* idx, DevStats* stats, cudaStream_t s,
-                               const int* count_dev = nullptr, const int* map = nullptr);
-// sequential in-block accept for flagged row i (see lc_fp64.cu)
-cudaError_t accept_step(int i, int f, double* R, int ldr, double* rn2, const double* hn2,
-                        double tol, double eta2, double* V, int ldv, int ncap, int P,
-                        DevStats* stats, DevStatus* st, int* accepted_rows, cudaStream_t s);
+                               const int* count_dev = nullptr, const int* map = nullptr, int measured = 0,
+                               float* rho2_flag = nullptr);
 cudaError_t zero_stats(DevStats* stats, int ncur, cudaStream_t s);
 
 // ------------------------------------------------------ mixed-precision path
@@ -160,6 +169,19 @@ cudaError_t split_rows(const double* V, int ldv, int r0, int r1, int P,
 cudaError_t bracket_mixed(const double* V, int d, int ldv, long long t0, int count,
                           __nv_bfloat16* Hhi, __nv_bfloat16* Hlo, int ldh, float* hn2,
                           cudaStream_t s);
+
+// screen noise probe: S rows in span(V) (S1 single basis rows, the rest
+// random 16-row combinations) as split BF16 candidate rows with their squared
+// norms; *nnz = S.  probe_eps: stats->eps2 = max rn2 / hn2 over the S rows,
+// stats->tau2 = clamp(kappa^2 eps2, tau_lo^2, tau_hi^2), eps_bits = run max.
+cudaError_t probe_rows(const double* V, int ldv, int N, int P, int S, int S1, unsigned long long seed,
+                       __nv_bfloat16* Chi, __nv_bfloat16* Clo, int ldc, float* hn2c, int* nnz, cudaStream_t s);
+cudaError_t probe_eps(const float* hn2c, const float* rn2, int S, DevStats* stats, float kappa, float tau_lo,
+                      float tau_hi, cudaStream_t s);
+// max |G - I| of the Gram rows [r0, r0 + rows) (rows x cols, row stride ldg)
+// into *out_bits (a double's bit pattern, atomicMax)
+cudaError_t defect_max(const double* G, int rows, int cols, int ldg, int r0, unsigned long long* out_bits,
+                       cudaStream_t s);
 
 // real 2d x 2d embeddings [[Hr, -Hi], [-Hi, -Hr]] of basis rows [r0, r1), split BF16
 // (perm: rows in the large-d bracket order, see lc_tcgen05.cu)
@@ -214,12 +236,17 @@ struct SplitGemmArgs {
   int epilogue;
   long long spin_cap;
   DevStatus* st;
+  int cfg;                         // tile configuration, 0 .. split_gemm_num_cfgs() - 1
 };
 cudaError_t split_gemm_tcgen05(const SplitGemmArgs& a, cudaStream_t s);
-// tile extents of split_gemm_tcgen05: N must be a multiple of split_gemm_tile_n(),
-// K of split_gemm_tile_k(), M of 128
+// tile extents of split_gemm_tcgen05: with N a multiple of split_gemm_tile_n(),
+// K of split_gemm_tile_k() and M of 128 every configuration applies;
+// the (int cfg) forms give one configuration's output tile width and k-slice
+int split_gemm_num_cfgs();
 int split_gemm_tile_n();
 int split_gemm_tile_k();
+int split_gemm_tile_n(int cfg);
+int split_gemm_tile_k(int cfg);
 bool tcgen05_available();
 
 }  // namespace lc

@@ -326,3 +326,96 @@ cudaError_t gather_candidates(const __nv_bfloat16* Hhi, const __nv_bfloat16* Hlo
 }
 
 }  // namespace lc
+
+// ------------------------------------------------------ screen noise probe
+// The split-BF16 screen cannot certify a residual below its own rounding
+// noise.  The probe measures that noise on vectors whose true residual is 0:
+// S1 single basis rows and S - S1 combinations of 16 basis rows with random
+// coefficients (both in span(V)), pushed through the same split and GEMMs as
+// the candidates.  Rows are picked and weighted by splitmix64 of (seed, row).
+namespace lc {
+namespace {
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+constexpr int PROBE_TERMS = 16;
+
+__global__ void __launch_bounds__(256) k_probe_rows(const double* __restrict__ V, int ldv, int N, int P, int S1,
+                                                    unsigned long long seed, __nv_bfloat16* __restrict__ Chi,
+                                                    __nv_bfloat16* __restrict__ Clo, int ldc,
+                                                    float* __restrict__ hn2c, int* __restrict__ nnz, int S) {
+  __shared__ int rows[PROBE_TERMS];
+  __shared__ double coef[PROBE_TERMS];
+  __shared__ double red[8];
+  const int j = blockIdx.x;
+  if (threadIdx.x < PROBE_TERMS) {
+    const unsigned long long h = splitmix64(seed ^ splitmix64(((unsigned long long)j << 8) | threadIdx.x));
+    rows[threadIdx.x] = (int)(h % (unsigned long long)N);
+    // coefficient uniform in [-1, -1/4] U [1/4, 1] (no near-cancellation of the combination)
+    const double u = (double)(h >> 11) * (1.0 / 9007199254740992.0);
+    coef[threadIdx.x] = (u < 0.5 ? -1.0 : 1.0) * (0.25 + 1.5 * fabs(u - 0.5));
+  }
+  __syncthreads();
+  const int T = j < S1 ? 1 : PROBE_TERMS;
+  double ss = 0.0;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    double x = 0.0;
+    for (int t = 0; t < T; ++t) x = fma(T == 1 ? 1.0 : coef[t], V[(long long)rows[t] * ldv + p], x);
+    __nv_bfloat16 hi, lo;
+    split_bf16(x, hi, lo);
+    Chi[(long long)j * ldc + p] = hi;
+    Clo[(long long)j * ldc + p] = lo;
+    ss = fma(x, x, ss);
+  }
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    hn2c[j] = (float)t;
+    if (j == 0) *nnz = S;
+  }
+}
+
+// eps^2 = max over probes of rn2 / hn2; tau^2 = clamp(kappa^2 eps^2, lo, hi)
+__global__ void k_probe_eps(const float* __restrict__ hn2c, const float* __restrict__ rn2, int S, DevStats* stats,
+                            float kappa2, float tau2_lo, float tau2_hi) {
+  __shared__ float wm[32];
+  float m = 0.f;
+  for (int j = threadIdx.x; j < S; j += blockDim.x)
+    if (hn2c[j] > 0.f) m = fmaxf(m, rn2[j] / hn2c[j]);
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float e2 = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) e2 = fmaxf(e2, wm[w]);
+    stats->eps2 = e2;
+    stats->tau2 = fminf(fmaxf(kappa2 * e2, tau2_lo), tau2_hi);
+    const double e = sqrt((double)e2);
+    atomicMax(&stats->eps_bits, (unsigned long long)__double_as_longlong(e));
+  }
+}
+
+}  // namespace
+
+cudaError_t probe_rows(const double* V, int ldv, int N, int P, int S, int S1, unsigned long long seed,
+                       __nv_bfloat16* Chi, __nv_bfloat16* Clo, int ldc, float* hn2c, int* nnz, cudaStream_t s) {
+  if (S <= 0 || N <= 0) return cudaSuccess;
+  k_probe_rows<<<S, 256, 0, s>>>(V, ldv, N, P, S1, seed, Chi, Clo, ldc, hn2c, nnz, S);
+  return cudaGetLastError();
+}
+
+cudaError_t probe_eps(const float* hn2c, const float* rn2, int S, DevStats* stats, float kappa, float tau_lo,
+                      float tau_hi, cudaStream_t s) {
+  k_probe_eps<<<1, 256, 0, s>>>(hn2c, rn2, S, stats, kappa * kappa, tau_lo * tau_lo, tau_hi * tau_hi);
+  return cudaGetLastError();
+}
+
+}  // namespace lc

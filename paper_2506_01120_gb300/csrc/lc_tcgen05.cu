@@ -184,8 +184,13 @@ struct GemmCfg {
   static constexpr int TMEM_COLS = BN_;
 };
 // 128 x 256 tiles with 32-wide k-slices: 25 % fewer operand bytes per MMA
-// flop than 128 x 128, and 4 x 48 KB stages in flight.
+// flop than 128 x 128, and 4 x 48 KB stages in flight (the default).  The
+// autotuner also tries 128 x 128 tiles with 64-wide slices in 3 stages and
+// with 32-wide slices in 6 stages; all three fill 192 KB of shared memory.
 using ScreenCfg = GemmCfg<256, 32, 4>;
+using ScreenCfg1 = GemmCfg<128, 64, 3>;
+using ScreenCfg2 = GemmCfg<128, 32, 6>;
+constexpr int kNumScreenCfgs = 3;
 
 struct GemmParams {
   int M, N, K;
@@ -425,8 +430,9 @@ bool tcgen05_available() {
   return major == 10 && minor == 3 && get_encode() != nullptr;
 }
 
-cudaError_t split_gemm_tcgen05(const SplitGemmArgs& a, cudaStream_t s) {
-  using G = ScreenCfg;
+namespace {
+template <class G>
+cudaError_t split_gemm_cfg(const SplitGemmArgs& a, cudaStream_t s) {
   if (a.M <= 0 || a.N <= 0) return cudaSuccess;
   if (a.M % BM || a.N % G::BN || a.K % G::BK || a.K <= 0) return cudaErrorInvalidValue;
   if ((a.lda % 8) || (a.ldb % 8)) return cudaErrorInvalidValue;   // TMA: 16-byte row strides
@@ -456,9 +462,22 @@ cudaError_t split_gemm_tcgen05(const SplitGemmArgs& a, cudaStream_t s) {
   k_split_gemm<G><<<ntiles, NTHREADS, G::SMEM, s>>>(mAhi, mAlo, mBhi, mBlo, p);
   return cudaGetLastError();
 }
+}  // namespace
 
-int split_gemm_tile_n() { return ScreenCfg::BN; }
-int split_gemm_tile_k() { return ScreenCfg::BK; }
+cudaError_t split_gemm_tcgen05(const SplitGemmArgs& a, cudaStream_t s) {
+  switch (a.cfg) {
+    case 0: return split_gemm_cfg<ScreenCfg>(a, s);
+    case 1: return split_gemm_cfg<ScreenCfg1>(a, s);
+    case 2: return split_gemm_cfg<ScreenCfg2>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int split_gemm_num_cfgs() { return kNumScreenCfgs; }
+int split_gemm_tile_n() { return std::max(ScreenCfg::BN, std::max(ScreenCfg1::BN, ScreenCfg2::BN)); }
+int split_gemm_tile_k() { return std::max(ScreenCfg::BK, std::max(ScreenCfg1::BK, ScreenCfg2::BK)); }
+int split_gemm_tile_n(int cfg) { return cfg == 1 ? ScreenCfg1::BN : (cfg == 2 ? ScreenCfg2::BN : ScreenCfg::BN); }
+int split_gemm_tile_k(int cfg) { return cfg == 1 ? ScreenCfg1::BK : (cfg == 2 ? ScreenCfg2::BK : ScreenCfg::BK); }
 
 }  // namespace lc
 

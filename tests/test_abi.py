@@ -44,7 +44,9 @@ def test_every_declared_symbol_is_exported(built_lib):
 def test_host_only_calls(built_lib):
     o = binding.make_options("fp64")
     assert o.precision == binding.LC_PREC_FP64
-    assert o.eta_abs == 1e-12 and o.tau_screen == 1e-3 and o.saturation_exit == 0
+    assert o.eta_abs == 1e-12 and o.tau_screen == 0.0 and o.saturation_exit == 0
+    assert o.screen_kappa == 10.0 and o.tol_mode == binding.LC_TOL_RELATIVE
+    assert o.autotune == 0 and o.ortho_check == 0
     assert binding.status_string(binding.LC_ERR_CAPACITY).startswith("basis capacity")
     assert binding.status_string(12345) == "unknown status"
     assert "sm_103a" in binding.version()
@@ -77,8 +79,8 @@ def test_struct_layouts_match_compiled_header(tmp_path):
 
 def test_struct_layouts_match_header():
     """ctypes mirrors of lc_options / lc_report have the C sizes."""
-    assert ctypes.sizeof(binding.Options) == 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4
-    assert ctypes.sizeof(binding.Report) == 8 * 8 + 8 * 5 + 8 + 8 + 8 + 8 + 8 * 6 + 4 * 2
+    assert ctypes.sizeof(binding.Options) == 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4 + 4 + 4 + 8
+    assert ctypes.sizeof(binding.Report) == 8 * 8 + 8 * 5 + 8 + 8 + 8 + 8 + 8 * 6 + 4 * 2 + 8 * 5 + 4 * 6
 
 
 def test_argument_errors_need_no_gpu(built_lib):

@@ -484,3 +484,18 @@ def test_planted_metric_mistake_is_caught(monkeypatch, mistake):
             return m
         monkeypatch.setattr(oc, "margin_report", first)
     assert not _metric_pins_pass()
+
+
+def test_absolute_and_relative_tolerance_readings():
+    """g2 = 1e4 iXI + 1e-3 iZZ has orthogonal part 1e-3 iZZ against g1 = iXI:
+    relative residual ~1e-7, absolute residual 1e-3.  At tol = 1e-6 the
+    relative reading rejects it (dimension 1: no pair to bracket), the absolute
+    one accepts it, and {XI, ZZ} bracket to YZ, closing to dimension 3."""
+    a, zz = inputs.generators_from_labels(["XI", "ZZ"])
+    g = np.stack([a, 1e4 * a + 1e-3 * zz])
+    assert oc.alg4_orthonormalization(g, 1e-6).dim == 1
+    r = oc.alg4_orthonormalization(g, 1e-6, tol_mode="absolute")
+    assert r.dim == 3
+    assert r.accepted_rel[1] == pytest.approx(1e-3 / np.linalg.norm([1e4, 1e-3]), rel=1e-6)
+    # a residual of 1e-3 at tol 1e-2 is rejected in both readings
+    assert oc.alg4_orthonormalization(g, 1e-2, tol_mode="absolute").dim == 1
