@@ -60,6 +60,12 @@ def parse():
     ap.add_argument("--pauli-only", action="store_true", help="run only the sparse Pauli-sum leg")
     ap.add_argument("--next-rows", action="store_true",
                     help="run only the Algorithm 2 / Algorithm 3 / resume timings and print them as one line")
+    ap.add_argument("--legs", default="fp64full,config5,config3,batched",
+                    help="comma list of the single-run workload legs after the timed steps "
+                         "(fp64full, config5, config3, batched; 'none' = skip)")
+    ap.add_argument("--batched-full", action="store_true",
+                    help="batched leg: full Algorithm 4 sweep per set instead of the saturation exit")
+    ap.add_argument("--autotune", type=int, default=0, help="lc_options.autotune for the timed steps")
     return ap.parse_args()
 
 
@@ -207,7 +213,8 @@ def run_reference(args, world, rank, pg):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / len(walls),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "d": 64, "k": 17, "tol": 1e-8},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             **host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -215,6 +222,8 @@ def run_reference(args, world, rank, pg):
 # ------------------------------------------------------------ GPU legs
 # Table 2 of the paper (many-core CPU, sparse Pauli sums): seconds per closure
 PAPER_TABLE2_S = {6: 429.0, 7: 2345.0}
+# issue-slot utilisation of k_pauli_screen1 measured by ncu (7-qubit chain)
+PAULI_SCREEN1_ISSUE_ACTIVE = 0.62
 # algorithmic bytes of the one-string screen (k_pauli_screen1) per candidate:
 # the two operand strings (16 B) and the flag (1 B), plus for anticommuting
 # pairs the index probe (string 8 B + head 4 B)
@@ -276,17 +285,150 @@ def pauli_leg(args, stream, peaks, peak_src):
             "value": cand / t, "unit": UNIT, "time_to_closure_s": t, "t_last_accept_s": reps[-1]["t_last_accept_s"],
             "phase_s": {"screen": t_screen, "accept": t_accept, "other": max(0.0, t - t_screen - t_accept)},
             "screen_launches": reps[0]["gemm_launches"], "gpu_launches": reps[0]["kernel_launches"],
-            "roofline": {"bound": "hbm", "achieved": gbs, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                         "frac": gbs / float(peaks["hbm_gbs"]), "traffic": None, "kernel": "k_pauli_screen1",
+            "roofline": {"bound": "issue", "achieved": gbs, "unit": "GB/s (algorithmic bytes, L2-resident)",
+                         "peak": None, "frac": None, "traffic": None, "kernel": "k_pauli_screen1",
                          "bytes_per_candidate": nbytes / screened if screened else None,
-                         "peak_source": f"hbm_gbs ({peak_src})",
-                         "note": "basis strings and index are L2-resident; only the flags reach HBM"},
+                         "issue_active_ncu": PAULI_SCREEN1_ISSUE_ACTIVE,
+                         "note": "the basis strings and the string index stay in L2 (ncu: 97 % L2 hit rate, "
+                                 "under 1 MB of DRAM traffic per launch); the kernel is bound by instruction "
+                                 "issue (ncu: issue slots busy, profiles/k_pauli_screen1_hea_n7.md), not by HBM"},
             "e2e": {"value": cand / te, "unit": UNIT, "time_to_closure_s": te,
                     "h2d_bytes_per_step": int(s.nbytes + c.nbytes + o.nbytes),
                     "d2h_bytes_per_step": int(D * 16 + (D + 1) * 8)},
             "paper_table2_cpu_s": PAPER_TABLE2_S.get(n),
         })
     return out
+
+
+def host_info():
+    """The host the oracle ran on: core counts and the BLAS thread setting."""
+    info = {"host_cores": os.cpu_count()}
+    try:
+        info["affinity_cores"] = len(os.sched_getaffinity(0))
+    except AttributeError:
+        pass
+    blas = None
+    try:
+        from threadpoolctl import threadpool_info
+        blas = [{"api": p.get("internal_api"), "threads": p.get("num_threads")} for p in threadpool_info()]
+    except Exception:
+        env = {k: os.environ[k] for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+               if k in os.environ}
+        blas = env or "library default (all cores)"
+    info["blas_threads"] = blas
+    return info
+
+
+def _closure_dev_timed(gd, tol, stream, **opts):
+    """One closure through lie_closure_dev, timed with CUDA events on its stream."""
+    import torch
+    from paper_2506_01120_gb300 import binding
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    r = binding.lie_closure_dev(gd, tol, stream=stream, **opts)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return r, a.elapsed_time(b) * 1e-3
+
+
+def fp64_full_leg(gd, tol, stream, mixed_s):
+    """The plain FP64 GPU form of the bench workload run to closure."""
+    r, t = _closure_dev_timed(gd, tol, stream, precision="fp64", profile=1)
+    cand = r.report["brackets_checked"] + r.report["generators_checked"]
+    return {"full_time_to_closure_s": t, "dim": r.dim, "candidates": cand, "brackets_per_s": cand / t,
+            "t_last_accept_s": r.report["t_last_accept_s"],
+            "phase_s": dict(zip(["brackets", "projection_gemm", "residual_gemm", "screen", "fp64_accept", "other"],
+                                r.report["t_phase_s"])),
+            "mixed_speedup_same_dim": t / mixed_s if mixed_s else None}
+
+
+def config5_leg(stream, window_mixed=2_000_000, window_fp64=20_000):
+    """su128_random2_d128 (d = 128, dim 16383, 134,193,155 candidates in the
+    full sweep): time to the saturation exit (labelled: not in the paper) for
+    both precisions, and a timed window of the saturated phase (resumed at the
+    pair (8192, 0) of the saturated basis) from which the full sweep's time
+    is extrapolated (labelled extrapolated)."""
+    import torch
+    from paper_2506_01120_gb300 import binding, inputs
+    g, _ = inputs.workload_generators("su128_random2_d128")
+    d, tol = g.shape[1], 1e-8
+    D = d * d - 1
+    full_cand = g.shape[0] + D * (D - 1) // 2
+    gd = torch.from_numpy(g).cuda()
+    B = torch.empty((D + 1, d, d), dtype=torch.complex128, device="cuda")
+    out = {"workload": "su128_random2_d128", "d": d, "closure_dim": D, "full_sweep_candidates": full_cand}
+    for prec, window in (("mixed", window_mixed), ("fp64", window_fp64)):
+        r, t = _closure_dev_timed(gd, tol, stream, precision=prec, saturation_exit=1, profile=1,
+                                  **({"basis_out": B} if prec == "mixed" else {}))
+        sat_cand = r.report["brackets_checked"] + r.report["generators_checked"]
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        w = binding.lie_closure_resume_dev(B, D, (8192, 0), tol, max_dim=D + 1, stream=stream, precision=prec,
+                                           max_candidates=window)
+        b.record(stream)
+        torch.cuda.synchronize()
+        tw = a.elapsed_time(b) * 1e-3
+        rate = w.report["brackets_checked"] / tw
+        out[prec] = {"saturation_exit": {"dim": r.dim, "candidates": sat_cand, "time_to_closure_s": t,
+                                         "phase_s": dict(zip(["brackets", "projection_gemm", "residual_gemm",
+                                                              "screen", "fp64_accept", "other"],
+                                                             r.report["t_phase_s"])),
+                                         "eps_screen": r.report["eps_screen"],
+                                         "tau_screen": r.report["tau_screen"], "n_gray": r.report["n_gray"],
+                                         "min_acc_rel_res": r.report["min_acc_rel_res"],
+                                         "min_acc_screen_rel_res": r.report["min_acc_screen_rel_res"]},
+                     "saturated_window": {"candidates": w.report["brackets_checked"], "time_s": tw,
+                                          "brackets_per_s": rate, "dim_after": w.dim,
+                                          "n_flagged": w.report["n_flagged"]},
+                     "full_sweep_time_s_extrapolated": t + (full_cand - sat_cand) / rate}
+    out["mixed_vs_fp64_saturation_exit_speedup"] = (out["fp64"]["saturation_exit"]["time_to_closure_s"] /
+                                                  out["mixed"]["saturation_exit"]["time_to_closure_s"])
+    out["mixed_vs_fp64_full_sweep_speedup_extrapolated"] = (out["fp64"]["full_sweep_time_s_extrapolated"] /
+                                                          out["mixed"]["full_sweep_time_s_extrapolated"])
+    del B
+    torch.cuda.empty_cache()
+    return out
+
+
+def config3_leg(stream, fp64_prefix=400):
+    """so20_chain_d1024 (d = 1024, dim 190): the full mixed closure, and the
+    FP64 and mixed forms on the same candidate prefix (the full FP64 closure
+    needs ~1.5e14 FP64 flop of brackets alone)."""
+    import torch
+    from paper_2506_01120_gb300 import inputs
+    g, _ = inputs.workload_generators("so20_chain_d1024")
+    gd = torch.from_numpy(g).cuda()
+    tol = 1e-8
+    r, t = _closure_dev_timed(gd, tol, stream, precision="mixed", max_dim=256, profile=1)
+    cand = r.report["brackets_checked"] + r.report["generators_checked"]
+    out = {"workload": "so20_chain_d1024", "dim": r.dim, "candidates": cand, "time_to_closure_s": t,
+           "brackets_per_s": cand / t,
+           "phase_s": dict(zip(["brackets", "projection_gemm", "residual_gemm", "screen", "fp64_accept", "other"],
+                               r.report["t_phase_s"]))}
+    rf, tf = _closure_dev_timed(gd, tol, stream, precision="fp64", max_dim=256, max_candidates=fp64_prefix)
+    rm, tm = _closure_dev_timed(gd, tol, stream, precision="mixed", max_dim=256, max_candidates=fp64_prefix)
+    out["prefix"] = {"candidates": fp64_prefix, "fp64_time_s": tf, "mixed_time_s": tm, "fp64_dim": rf.dim,
+                     "mixed_dim": rm.dim}
+    return out
+
+
+def batched_leg(full: bool):
+    """The 256-set batched workload (seed 1120) through lie_closure_batched;
+    per-set dimensions checked against the closed form / exact Pauli closure."""
+    import oracle.closure as oc
+    from paper_2506_01120_gb300 import binding, inputs
+    sets = inputs.batched_sets(256, seed=1120)
+    gens = [x["generators"] for x in sets]
+    t0 = time.perf_counter()
+    dims, stat, _, reps = binding.lie_closure_batched(gens, 1e-8, saturation_exit=0 if full else 1)
+    t = time.perf_counter() - t0
+    ok = all(st == 0 for st in stat)
+    exact = all(dim == (len(oc.pauli_closure(x["labels"])) if x["kind"] == "pauli" else x["d"] ** 2 - 1)
+                for x, dim in zip(sets, dims))
+    cand = sum(r["brackets_checked"] + r["generators_checked"] for r in reps)
+    return {"workload": "batched256_d8to64", "sets": len(sets), "mode": "full sweep" if full else
+            "saturation exit (labelled; not in the paper)", "time_s": t, "candidates": cand,
+            "brackets_per_s": cand / t, "all_ok": ok, "all_dims_exact": exact}
 
 
 def next_rows_leg():
@@ -362,6 +504,8 @@ def run_ours(args, world, rank, local, pg):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
     opts = dict(precision="mixed", profile=1)
+    if args.autotune:
+        opts["autotune"] = args.autotune
     if args.block_k:
         opts["block_k"] = args.block_k
     if args.tau:
@@ -451,12 +595,28 @@ def run_ours(args, world, rank, local, pg):
 
     sparse = pauli_leg(args, stream, peaks, peak_src) if args.pauli_steps > 0 else None
 
+    # single-run legs on the other workloads (not part of the timed steps)
+    legs = set(x for x in args.legs.split(",") if x and x != "none")
+    workloads = {}
+    mixed_step_s = total / args.steps
+    if "fp64full" in legs:
+        fp64_full = fp64_full_leg(gd, tol, stream, mixed_step_s)
+        if fp64 is None:
+            fp64 = {}
+        fp64.update(fp64_full)
+    if "config5" in legs:
+        workloads["su128_random2_d128"] = config5_leg(stream)
+    if "config3" in legs:
+        workloads["so20_chain_d1024"] = config3_leg(stream)
+    if "batched" in legs:
+        workloads["batched256_d8to64"] = batched_leg(args.batched_full)
+
     cpu = None
     if rank == 0 and args.cpu_seconds > 0:
         rate, c, w, cores = oracle_sample(args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{c} candidates in {w:.1f} s, oracle resumed at the saturated state of {WORKLOAD} "
-                         f"(|V|=4095, cursor l=2000)"}
+                         f"(|V|=4095, cursor l=2000)", **host_info()}
 
     if rank != 0:
         return
@@ -481,13 +641,18 @@ def run_ours(args, world, rank, local, pg):
         "e2e": e2e,
         "saturation_exit": sat,
         "fp64_gpu": fp64,
+        "workloads": workloads or None,
         "sparse_pauli": sparse,
         "cpu_baseline": cpu,
         "gpu_launches": int(sum(rep["kernel_launches"] for rep in reports)),
         "clocks": clocks,
         "screen": {"n_flagged": rep0["n_flagged"], "n_nonzero": rep0["n_nonzero"],
+                   "tau_screen": rep0["tau_screen"], "eps_screen": rep0["eps_screen"], "n_gray": rep0["n_gray"],
                    "max_screen_rej_rel_res": rep0["max_screen_rej_rel_res"],
+                   "min_acc_screen_rel_res": rep0["min_acc_screen_rel_res"],
                    "min_acc_rel_res": rep0["min_acc_rel_res"], "max_rej_rel_res": rep0["max_rej_rel_res"]},
+        "tiles": {"block_k": rep0["block_k_used"], "block_k_growth": rep0["block_k_growth_used"],
+                  "gemm_tile": [128, rep0["gemm_tile_n"], rep0["gemm_tile_k"]], "autotuned": rep0["autotuned"]},
     }
     print(json.dumps(line), flush=True)
 

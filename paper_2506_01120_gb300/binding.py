@@ -283,6 +283,32 @@ def lie_closure_dev(generators, tol: float, max_dim: int | None = None, basis_ou
     return ClosureResult(int(dim.value), None, st, rep.as_dict())
 
 
+def lie_closure_resume_dev(basis, n_in: int, cursor, tol: float, max_dim: int | None = None, basis_out=None,
+                           stream=None, check: bool = True, precision="mixed", **opts) -> ClosureResult:
+    """``lie_closure_resume`` on device tensors: ``basis`` is a contiguous
+    (>= n_in, d, d) complex128 CUDA tensor whose first n_in elements are the
+    saved basis; ``basis_out`` (optional) a (max_dim, d, d) device tensor."""
+    import torch
+    b = basis
+    if not (b.is_cuda and b.dtype == torch.complex128 and b.is_contiguous() and b.dim() == 3 and b.shape[0] >= n_in):
+        raise ValueError("basis must be a contiguous (>= n_in, d, d) complex128 CUDA tensor")
+    d = b.shape[1]
+    cap = int(max_dim) if max_dim is not None else d * d
+    if basis_out is not None:
+        if not (basis_out.is_cuda and basis_out.dtype == torch.complex128 and basis_out.is_contiguous()
+                and basis_out.shape[0] >= cap and tuple(basis_out.shape[1:]) == (d, d)):
+            raise ValueError("basis_out must be a contiguous (max_dim, d, d) complex128 CUDA tensor")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    dim = ctypes.c_longlong(0)
+    rep = Report()
+    o = make_options(precision, **opts)
+    st = lib().lie_closure_resume_dev(b.data_ptr(), int(n_in), int(cursor[0]), int(cursor[1]), d, float(tol),
+                                      basis_out.data_ptr() if basis_out is not None else None, ctypes.byref(dim),
+                                      cap, ctypes.byref(o), ctypes.byref(rep), ctypes.c_void_p(s.cuda_stream))
+    _check(st, check)
+    return ClosureResult(int(dim.value), None, st, rep.as_dict())
+
+
 def lie_closure_batched(generator_sets, tol: float, max_dims=None, return_basis: bool = False,
                         precision="mixed", **opts):
     """Algorithm 4 on many independent sets; returns (dims, statuses, bases, reports)."""
