@@ -574,9 +574,10 @@ namespace {
 
 template <int D>
 struct BrCfg {
-  // MMA rows: the first D rows of E_l.  For D = 64 the M = 64 shape is used;
-  // its accumulator row i sits in TMEM lane 32 (i / 16) + i % 16.
-  static constexpr int MM = D == 64 ? 64 : 128;
+  // MMA rows: the first D rows of E_l.  For D <= 64 the M = 64 shape is used
+  // (for D = 32 its last 32 rows are not needed); its accumulator row i sits
+  // in TMEM lane 32 (i / 16) + i % 16.
+  static constexpr int MM = D <= 64 ? 64 : 128;
   static constexpr int R = 2 * D;              // rows of E = MMA N = K extent
   static constexpr int TILE = R * 64 * 2;       // one R x 64 BF16 tile
   static constexpr int STAGE = 4 * TILE;        // El hi/lo, Em hi/lo
@@ -677,7 +678,7 @@ __global__ void __launch_bounds__(128, 1)
   const bool run = !(*(volatile int*)&abort_flag);
   // output row of this lane (M = 64: lanes 0-15 of each warp quarter)
   const int j = C::MM == 64 ? warp * 16 + (lane & 15) : warp * 32 + lane;
-  const bool mine = C::MM == 64 ? lane < 16 : j < D;
+  const bool mine = (C::MM == 64 ? lane < 16 : true) && j < D;
   float ss = 0.f;
   if (run && (C::MM == 64 || warp * 32 < D)) {         // warp-uniform
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
@@ -734,12 +735,13 @@ cudaError_t launch_bracket_tc(const __nv_bfloat16* Ehi, const __nv_bfloat16* Elo
 
 }  // namespace
 
-bool bracket_tc_supported(int d) { return d == 64 || d == 128; }
+bool bracket_tc_supported(int d) { return d == 32 || d == 64 || d == 128; }
 
 cudaError_t bracket_tc(const __nv_bfloat16* Ehi, const __nv_bfloat16* Elo, long long nelems, int d, long long t0,
                        int count, __nv_bfloat16* Hhi, __nv_bfloat16* Hlo, int ldh, float* hn2, long long spin_cap,
                        DevStatus* st, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
+  if (d == 32) return launch_bracket_tc<32>(Ehi, Elo, nelems, t0, count, Hhi, Hlo, ldh, hn2, spin_cap, st, s);
   if (d == 64) return launch_bracket_tc<64>(Ehi, Elo, nelems, t0, count, Hhi, Hlo, ldh, hn2, spin_cap, st, s);
   if (d == 128) return launch_bracket_tc<128>(Ehi, Elo, nelems, t0, count, Hhi, Hlo, ldh, hn2, spin_cap, st, s);
   return cudaErrorInvalidValue;
@@ -855,47 +857,116 @@ extern "C" LC_API int lc_split_gemm_f32_noalloc(const float* A, const float* B, 
 }
 
 // ------------------------------------------- d = 64 brackets from [Hr; Hi]
-// Each basis element is also stored as P = [Hr; Hi] (2d x d rows, split
-// BF16): half the bytes of the 2d x 2d embedding.  With A = H_l, B = H_m and
-// the tcgen05 product MMA(X, Y) = X Y^T (both operands row-major d x d),
-// Hr^T = Hr and Hi^T = -Hi give
-//   Re(AB - BA) =  MMA(Ar, Br) + MMA(Ai, Bi) - MMA(Br, Ar) - MMA(Bi, Ai)
-//   Im(AB - BA) = -MMA(Ar, Bi) + MMA(Ai, Br) + MMA(Br, Ai) - MMA(Bi, Ar)
-// (each term three split MMAs; the minus signs use the negate-A bit), into two
-// 64-column TMEM accumulators.  M = 64 shape: row i in lane 32 (i/16) + i%16.
+// Each basis element is also stored as Q = [Hr; Hi] (2d x d rows, split
+// BF16).  For a pair (l, m) with A = H_l and B = H_m the kernel forms one
+// complex product D = B A on the tensor cores and takes the bracket from D and
+// its conjugate transpose: A and B are Hermitian, so (B A)^dagger = A B and
+// [V_l, V_m] = [iA, iB] = -(AB - BA) = D - D^dagger.  With the tcgen05 product
+// MMA(X, Y) = X Y^T and Hr^T = Hr, Hi^T = -Hi:
+//   Re D = MMA(Br, Ar) + MMA(Bi, Ai),   Im D = -MMA(Br, Ai) + MMA(Bi, Ar),
+// one accumulator of 128 columns [Re D | Im D] from two 64-wide k-chunks:
+//   chunk 0: X = Br, Y = [Ar; -Ai];   chunk 1: X = Bi, Y = [Ai; Ar].
+// Two pairs (l, m), (l, m + 1) share A and so Y: their B operands fill the
+// 128 rows of X, the full M = 128 instruction shape.
+// Persistent CTAs: CTA c takes a contiguous share of the block's pairs in
+// pair order, so consecutive units mostly keep l and Y stays in shared
+// memory (a new l reloads it).  Warp 0 streams Y and X with TMA and negates
+// the -Ai half of Y in shared memory; warp 1 issues a unit's 24 MMAs into one
+// of two TMEM accumulators; warps 2-5 copy an accumulator into a padded
+// shared tile T (row r = TMEM lane r) and write packed row j of each bracket
+// from row j and column j of D:
+//   S[j][k] = s2 (Im D[j][k] + Im D[k][j])   (k > j)
+//   S[j][j] = s1 2 Im D[j][j]
+//   S[j][k] = s2 (Re D[j][k] - Re D[k][j])   (k < j)
+// with s1 = 1/sqrt(d), s2 = sqrt(2/d).  Every wait is bounded; a wait that
+// runs out (or sees another role's abort) records LC_ERR_TIMEOUT, the roles
+// leave their loops together, issued copies and MMAs are drained, and TMEM is
+// released.
 namespace lc {
 namespace {
 
 constexpr int Q_D = 64;
-constexpr int Q_TILE = Q_D * Q_D * 2;          // one d x d BF16 tile (8 KB)
-constexpr int Q_STAGE = 8 * Q_TILE;           // Ar, Ai, Br, Bi in hi and lo
-constexpr int Q_SMEM = Q_STAGE + 1024;
-constexpr int Q_TMEM = 128;
+constexpr int QP_TILE = 128 * 64 * 2;     // one 128-row x 64-column BF16 tile (16 KB)
+constexpr int QP_HALF = QP_TILE / 2;      // 64 rows (8 KB): one TMA box
+constexpr int QP_Y = 4 * QP_TILE;         // Y0hi, Y0lo, Y1hi, Y1lo
+constexpr int QP_X = 4 * QP_TILE;         // X0hi, X0lo, X1hi, X1lo  (X0 = Br, X1 = Bi)
+constexpr int QP_TLD = 129;               // padded row stride of T (floats): conflict-free rows and columns
+constexpr int QP_T = 128 * QP_TLD * 4;
+constexpr int QP_SMEM = QP_Y + QP_X + QP_T + 1024;
+constexpr int QP_TMEM = 256;              // two 128-column accumulators
+constexpr int QP_THREADS = 192;
 
-__global__ void __launch_bounds__(128, 1)
-    k_bracket_q64(const __grid_constant__ CUtensorMap mQhi, const __grid_constant__ CUtensorMap mQlo, long long t0,
-                  __nv_bfloat16* __restrict__ Hhi, __nv_bfloat16* __restrict__ Hlo, int ldh, float* __restrict__ hn2,
-                  uint64_t limit_ns, DevStatus* st) {
-  extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar, done_bar;
-  __shared__ uint32_t tmem_slot;
-  __shared__ int abort_flag;
-  __shared__ float red[4];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int pair = blockIdx.x;
+// Bounded wait that also gives up as soon as another role has aborted.
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, uint64_t limit_ns,
+                                              volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0 && (*abort_flag || globaltimer_ns() - t0 > limit_ns)) return false;
+  }
+}
+
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Units of one or two pairs sharing l, walked identically by every role.
+struct UnitWalk {
+  long long t, tend;
   int l, m;
-  pair_from_index(t0 + pair, &l, &m);
+  __device__ void start(long long t_begin, long long t_end) {
+    t = t_begin;
+    tend = t_end;
+    pair_from_index(t, &l, &m);
+  }
+  __device__ bool more() const { return t < tend; }
+  __device__ int size() const { return (t + 1 < tend && m + 1 < l) ? 2 : 1; }
+  __device__ void next(int n) {
+    t += n;
+    m += n;
+    if (m >= l) {
+      ++l;
+      m = 0;
+    }
+  }
+};
+
+__global__ void __launch_bounds__(QP_THREADS, 1)
+    k_bracket_q64(const __grid_constant__ CUtensorMap mQhi, const __grid_constant__ CUtensorMap mQlo, long long t0,
+                  int count, __nv_bfloat16* __restrict__ Hhi, __nv_bfloat16* __restrict__ Hlo, int ldh,
+                  float* __restrict__ hn2, uint64_t limit_ns, DevStatus* st) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t x_full, x_empty, y_full, y_ready, done_bar;
+  __shared__ __align__(8) uint64_t t_full[2], t_empty[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag, epi_abort;
+  const long long p0 = (long long)count * blockIdx.x / gridDim.x;
+  const long long p1 = (long long)count * (blockIdx.x + 1) / gridDim.x;
+  if (p0 >= p1) return;                                   // whole CTA: no pairs
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* Y = smem;
+  uint8_t* X = smem + QP_Y;
+  float* T = reinterpret_cast<float*>(smem + QP_Y + QP_X);
   if (threadIdx.x == 0) {
-    mbar_init(&full_bar, 1);
+    mbar_init(&x_full, 1);
+    mbar_init(&x_empty, 1);
+    mbar_init(&y_full, 1);
+    mbar_init(&y_ready, 1);
     mbar_init(&done_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&t_full[b], 1);
+      mbar_init(&t_empty[b], 1);
+    }
     abort_flag = 0;
+    epi_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (warp == 2) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(Q_TMEM)
+                 "r"(QP_TMEM)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -903,97 +974,192 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  // shared-memory tiles: [Ar Ai Br Bi] hi, then [Ar Ai Br Bi] lo
-  if (warp == 0 && lane == 0) {
-    mbar_expect_tx(&full_bar, Q_STAGE);
-    tma_load_2d(smem + 0 * Q_TILE, &mQhi, &full_bar, 0, l * 2 * Q_D);
-    tma_load_2d(smem + 1 * Q_TILE, &mQhi, &full_bar, 0, l * 2 * Q_D + Q_D);
-    tma_load_2d(smem + 2 * Q_TILE, &mQhi, &full_bar, 0, m * 2 * Q_D);
-    tma_load_2d(smem + 3 * Q_TILE, &mQhi, &full_bar, 0, m * 2 * Q_D + Q_D);
-    tma_load_2d(smem + 4 * Q_TILE, &mQlo, &full_bar, 0, l * 2 * Q_D);
-    tma_load_2d(smem + 5 * Q_TILE, &mQlo, &full_bar, 0, l * 2 * Q_D + Q_D);
-    tma_load_2d(smem + 6 * Q_TILE, &mQlo, &full_bar, 0, m * 2 * Q_D);
-    tma_load_2d(smem + 7 * Q_TILE, &mQlo, &full_bar, 0, m * 2 * Q_D + Q_D);
-    mbar_wait_bounded(&full_bar, 0u, kDrainNs);       // copies land before anything can leave
-  } else if (warp == 1 && lane == 0) {
-    constexpr uint32_t id = make_idesc_bf16(64, Q_D);
-    constexpr uint32_t idn = id | (1u << 13);        // negate A
-    if (!mbar_wait_bounded(&full_bar, 0u, limit_ns)) {
-      record_timeout(st, SITE_GEMM_MMA_WAIT, pair);
-      abort_flag = 1;
-    } else {
-      tc_fence_after();
-      const uint32_t base = smem_u32(smem);
-      const uint32_t ARh = base, AIh = base + Q_TILE, BRh = base + 2 * Q_TILE, BIh = base + 3 * Q_TILE;
-      const uint32_t lo = 4 * Q_TILE;
-      const uint32_t tre = tmem, tim = tmem + 64;
-      const uint32_t X[8] = {ARh, AIh, BRh, BIh, ARh, AIh, BRh, BIh};
-      const uint32_t Y[8] = {BRh, BIh, ARh, AIh, BIh, BRh, AIh, ARh};
-      const uint32_t NG[8] = {0, 0, 1, 1, 1, 0, 0, 1};
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const uint32_t dsc = NG[t] ? idn : id;
-        const uint32_t td = t < 4 ? tre : tim;
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint32_t off = kk * 32;
-          const uint64_t xh = make_sw128_desc(X[t] + off), xl = make_sw128_desc(X[t] + lo + off);
-          const uint64_t yh = make_sw128_desc(Y[t] + off), yl = make_sw128_desc(Y[t] + lo + off);
-          mma_bf16(td, xh, yh, dsc, ((t & 3) | kk) ? 1u : 0u);   // first product of each accumulator starts it
-          mma_bf16(td, xh, yl, dsc, 1u);
-          mma_bf16(td, xl, yh, dsc, 1u);
+  volatile int* ab = &abort_flag;
+  const long long tb = t0 + p0, te = t0 + p1;
+
+  if (warp == 0) {
+    // ---------------- producer: Y per new l (then negate -Ai), X per unit
+    UnitWalk w;
+    w.start(tb, te);
+    int cur_l = -1, ny = 0, nx = 0;
+    while (w.more()) {
+      const int n = w.size();
+      // the single X stage (and Y) is free once the previous unit's MMAs retired
+      if (nx > 0 && !wait_or_abort(&x_empty, (uint32_t)(nx - 1) & 1u, limit_ns, ab)) {
+        if (lane == 0) record_timeout(st, SITE_GEMM_TMA_WAIT, nx);
+        *ab = 1;
+        break;
+      }
+      if (w.l != cur_l) {
+        if (lane == 0) {
+          const int ra = w.l * 2 * Q_D, ri = ra + Q_D;
+          mbar_expect_tx(&y_full, QP_Y);
+          tma_load_2d(Y + 0 * QP_TILE, &mQhi, &y_full, 0, ra);
+          tma_load_2d(Y + 0 * QP_TILE + QP_HALF, &mQhi, &y_full, 0, ri);
+          tma_load_2d(Y + 1 * QP_TILE, &mQlo, &y_full, 0, ra);
+          tma_load_2d(Y + 1 * QP_TILE + QP_HALF, &mQlo, &y_full, 0, ri);
+          tma_load_2d(Y + 2 * QP_TILE, &mQhi, &y_full, 0, ri);
+          tma_load_2d(Y + 2 * QP_TILE + QP_HALF, &mQhi, &y_full, 0, ra);
+          tma_load_2d(Y + 3 * QP_TILE, &mQlo, &y_full, 0, ri);
+          tma_load_2d(Y + 3 * QP_TILE + QP_HALF, &mQlo, &y_full, 0, ra);
+        }
+        __syncwarp();
+        ++ny;
+        if (!wait_or_abort(&y_full, (uint32_t)(ny - 1) & 1u, limit_ns, ab)) {
+          if (lane == 0) record_timeout(st, SITE_GEMM_TMA_WAIT, -ny);
+          *ab = 1;
+          break;
+        }
+        // Y0 = [Ar; -Ai]: flip the sign bits of the lower half (hi and lo)
+        uint32_t* w0 = reinterpret_cast<uint32_t*>(Y + QP_HALF);
+        uint32_t* w1 = reinterpret_cast<uint32_t*>(Y + QP_TILE + QP_HALF);
+        for (int i = lane; i < QP_HALF / 4; i += 32) {
+          w0[i] ^= 0x80008000u;
+          w1[i] ^= 0x80008000u;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor core
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&y_ready);
+        cur_l = w.l;
+      }
+      if (lane == 0) {
+        mbar_expect_tx(&x_full, n * 4 * QP_HALF);
+        for (int q = 0; q < n; ++q) {
+          const int rr = (w.m + q) * 2 * Q_D, rI = rr + Q_D;
+          tma_load_2d(X + 0 * QP_TILE + q * QP_HALF, &mQhi, &x_full, 0, rr);
+          tma_load_2d(X + 1 * QP_TILE + q * QP_HALF, &mQlo, &x_full, 0, rr);
+          tma_load_2d(X + 2 * QP_TILE + q * QP_HALF, &mQhi, &x_full, 0, rI);
+          tma_load_2d(X + 3 * QP_TILE + q * QP_HALF, &mQlo, &x_full, 0, rI);
         }
       }
+      __syncwarp();
+      ++nx;
+      w.next(n);
     }
-    mma_commit(&done_bar);
+    // drain: no copy may still be writing shared memory when the CTA leaves
+    if (nx > 0) mbar_wait_bounded(&x_full, (uint32_t)(nx - 1) & 1u, kDrainNs);
+    if (ny > 0) mbar_wait_bounded(&y_full, (uint32_t)(ny - 1) & 1u, kDrainNs);
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc_bf16(128, 128);
+      UnitWalk w;
+      w.start(tb, te);
+      int cur_l = -1, ny = 0, u = 0;
+      while (w.more()) {
+        const int n = w.size();
+        const int b = u & 1;
+        bool ok = wait_or_abort(&x_full, (uint32_t)u & 1u, limit_ns, ab);
+        if (ok && w.l != cur_l) {
+          ok = wait_or_abort(&y_ready, (uint32_t)ny & 1u, limit_ns, ab);
+          ++ny;
+          cur_l = w.l;
+        }
+        if (ok && u >= 2) ok = wait_or_abort(&t_empty[b], (uint32_t)((u >> 1) - 1) & 1u, limit_ns, ab);
+        if (!ok) {
+          record_timeout(st, SITE_GEMM_MMA_WAIT, u);
+          *ab = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(b * 128);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const uint32_t xh = smem_u32(X + (2 * c) * QP_TILE), xl = xh + QP_TILE;
+          const uint32_t yh = smem_u32(Y + (2 * c) * QP_TILE), yl = yh + QP_TILE;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t off = kk * 32;
+            const uint64_t dxh = make_sw128_desc(xh + off), dxl = make_sw128_desc(xl + off);
+            const uint64_t dyh = make_sw128_desc(yh + off), dyl = make_sw128_desc(yl + off);
+            mma_bf16(d, dxh, dyh, idesc, (c | kk) ? 1u : 0u);
+            mma_bf16(d, dxh, dyl, idesc, 1u);
+            mma_bf16(d, dxl, dyh, idesc, 1u);
+          }
+        }
+        mma_commit(&x_empty);        // X (and Y) may be overwritten once these retire
+        mma_commit(&t_full[b]);      // accumulator b complete
+        ++u;
+        w.next(n);
+      }
+      mma_commit(&done_bar);         // every issued MMA has retired when this arrives
+    }
+  } else {
+    // ---------------- epilogue: warps 2-5, TMEM lane quarter q = warp % 4
+    const int q = warp & 3;
+    const int r = q * 32 + lane;                 // accumulator row: pair r / 64, row j = r % 64
+    const int p = r >> 6, j = r & 63;
+    const float s1 = rsqrtf((float)Q_D), s2 = sqrtf(2.f / (float)Q_D);
+    UnitWalk w;
+    w.start(tb, te);
+    int u = 0;
+    while (w.more()) {
+      const int n = w.size();
+      const int b = u & 1;
+      if (!wait_or_abort(&t_full[b], (uint32_t)(u >> 1) & 1u, limit_ns, ab)) epi_abort = 1;
+      named_bar_sync(1, 128);
+      if (*(volatile int*)&epi_abort) break;     // uniform: only written before this barrier
+      tc_fence_after();
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 128);
+      float* Tr = T + r * QP_TLD;
+#pragma unroll 1
+      for (int c = 0; c < 128; c += 32) {
+        float v[32];
+        tmem_ld_32cols(taddr + (uint32_t)c, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) Tr[c + i] = v[i];
+      }
+      tc_fence_before();
+      named_bar_sync(1, 128);                    // T complete; accumulator b free
+      if (threadIdx.x == 64) mbar_arrive(&t_empty[b]);
+      if (p < n) {
+        const long long pidx = w.t + p - t0;     // position of the pair in the block
+        const float* Tc = T + (p * 64) * QP_TLD + j;   // column j of this pair's D
+        __nv_bfloat16* oh = Hhi + pidx * ldh + (long long)j * Q_D;
+        __nv_bfloat16* ol = Hlo + pidx * ldh + (long long)j * Q_D;
+        float ss = 0.f;
+#pragma unroll 1
+        for (int c = 0; c < Q_D; c += 32) {
+          __align__(16) __nv_bfloat16 hi[32], lo[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int k = c + i;
+            const float re_jk = Tr[k], im_jk = Tr[Q_D + k];
+            const float re_kj = Tc[k * QP_TLD], im_kj = Tc[k * QP_TLD + Q_D];
+            const float v = (k > j) ? s2 * (im_jk + im_kj) : ((k == j) ? s1 * (im_jk + im_kj) : s2 * (re_jk - re_kj));
+            ss = fmaf(v, v, ss);
+            hi[i] = __float2bfloat16_rn(v);
+            lo[i] = __float2bfloat16_rn(v - __bfloat162float(hi[i]));
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            reinterpret_cast<uint4*>(oh + c)[i] = reinterpret_cast<const uint4*>(hi)[i];
+            reinterpret_cast<uint4*>(ol + c)[i] = reinterpret_cast<const uint4*>(lo)[i];
+          }
+        }
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (lane == 0) atomicAdd(&hn2[pidx], ss);
+      }
+      named_bar_sync(1, 128);                    // T may be overwritten by the next unit
+      ++u;
+      w.next(n);
+    }
+    if (*(volatile int*)&epi_abort) {
+      if (threadIdx.x == 64) record_timeout(st, SITE_GEMM_EPI_WAIT, u);
+      *ab = 1;
+    }
   }
+  // ---------------- teardown: every issued MMA retired before TMEM is released
   __syncwarp();
-  const bool have = mbar_wait_bounded(&done_bar, 0u, limit_ns);
-  if (!have) {
-    record_timeout(st, SITE_GEMM_EPI_WAIT, pair);
-    atomicExch(&abort_flag, 1);
+  if (!mbar_wait_bounded(&done_bar, 0u, limit_ns)) {
+    record_timeout(st, SITE_GEMM_EPI_WAIT, -1);
     mbar_wait_bounded(&done_bar, 0u, kDrainNs);
   }
-  __syncthreads();
-  tc_fence_after();
-  const bool run = !(*(volatile int*)&abort_flag);
-  const int j = warp * 16 + (lane & 15);               // M = 64: lanes 0-15 of each quarter
-  const bool mine = lane < 16;
-  float ss = 0.f;
-  if (run) {
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    const float s1 = rsqrtf((float)Q_D), s2 = sqrtf(2.f / (float)Q_D);
-    __nv_bfloat16* oh = Hhi + (long long)pair * ldh + (long long)j * Q_D;
-    __nv_bfloat16* ol = Hlo + (long long)pair * ldh + (long long)j * Q_D;
-    for (int c = 0; c < Q_D; c += 32) {
-      float re[32], im[32];
-      tmem_ld_32cols(trow + (uint32_t)c, re);
-      tmem_ld_32cols(trow + (uint32_t)(64 + c), im);
-      if (!mine) continue;
-      __align__(16) __nv_bfloat16 hi[32], lov[32];
-#pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int k = c + i;
-        const float v = (k > j) ? -s2 * im[i] : ((k == j) ? -s1 * im[i] : -s2 * re[i]);
-        ss = fmaf(v, v, ss);
-        hi[i] = __float2bfloat16_rn(v);
-        lov[i] = __float2bfloat16_rn(v - __bfloat162float(hi[i]));
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        reinterpret_cast<uint4*>(oh + c)[i] = reinterpret_cast<const uint4*>(hi)[i];
-        reinterpret_cast<uint4*>(ol + c)[i] = reinterpret_cast<const uint4*>(lov)[i];
-      }
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-  if (lane == 0) red[warp] = ss;
   tc_fence_before();
   __syncthreads();
-  if (threadIdx.x == 0 && run) hn2[pair] = red[0] + red[1] + red[2] + red[3];
-  if (warp == 2) {
+  if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Q_TMEM) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(QP_TMEM) : "memory");
   }
 }
 
@@ -1006,10 +1172,14 @@ cudaError_t bracket_q64(const __nv_bfloat16* Qhi, const __nv_bfloat16* Qlo, long
   CUtensorMap mh, ml;
   if (!make_map(&mh, Qhi, nelems * 2 * Q_D, Q_D, Q_D, Q_D) || !make_map(&ml, Qlo, nelems * 2 * Q_D, Q_D, Q_D, Q_D))
     return cudaErrorInvalidValue;
-  const cudaError_t attr_err = smem_optin(reinterpret_cast<const void*>(k_bracket_q64), Q_SMEM);
+  const cudaError_t attr_err = smem_optin(reinterpret_cast<const void*>(k_bracket_q64), QP_SMEM);
   if (attr_err != cudaSuccess) return attr_err;
+  cudaError_t e = cudaMemsetAsync(hn2, 0, sizeof(float) * count, s);
+  if (e != cudaSuccess) return e;
   const uint64_t lim = spin_cap > 0 ? (uint64_t)spin_cap : 4000000000ull;
-  k_bracket_q64<<<count, 128, Q_SMEM, s>>>(mh, ml, t0, Hhi, Hlo, ldh, hn2, lim, st);
+  // one CTA per SM, each with a contiguous share of at least one unit
+  const int G = std::max(1, std::min(device_sm_count(), (count + 1) / 2));
+  k_bracket_q64<<<G, QP_THREADS, QP_SMEM, s>>>(mh, ml, t0, count, Hhi, Hlo, ldh, hn2, lim, st);
   return cudaGetLastError();
 }
 

@@ -1,7 +1,8 @@
 """Element-by-element oracle parity of the tensor-core bracket kernels.
 
-The mixed path forms brackets on the tensor cores for d = 64 (k_bracket_q64),
-d = 128 (k_bracket_tc<128>) and d >= 256 (k_bracket_big).  Full closures at
+The mixed path forms brackets on the tensor cores for d = 32
+(k_bracket_tc<32>), d = 64 (k_bracket_q64), d = 128 (k_bracket_tc<128>) and
+d >= 256 (k_bracket_big).  Full closures at
 those sizes are out of the oracle's reach, so these tests stop both sides
 after the same number of bracket candidates (the pair order is the same, so
 the two runs check the same candidates) and compare the bases element by
@@ -38,6 +39,23 @@ def _prefix_case(g, tol, ncand, max_dim):
     np.testing.assert_allclose(res.basis, ref.basis, atol=1e-11, rtol=0)
     assert oc.ortho_defect(res.basis) < 1e-12
     return res, ref
+
+
+def test_random_pair_d32_to_saturation():
+    """k_bracket_tc<32> (M = 64 shape, half its rows used): a random traceless
+    pair at d = 32 to su(32) (1023) with the saturation exit on both sides,
+    every element compared."""
+    g = inputs.random_set(32, 2, seed=32)
+    ref = oc.alg4_orthonormalization(g, 1e-8, saturation_exit=True)
+    res = binding.lie_closure(g, 1e-8, precision="mixed", saturation_exit=1)
+    assert res.dim == ref.dim == 1023
+    np.testing.assert_allclose(res.basis, ref.basis, atol=1e-11, rtol=0)
+
+
+def test_prefix_su32_chain_d32():
+    """k_bracket_tc<32> on the Pauli chain (zero and duplicate brackets)."""
+    g = inputs.generators_from_labels(inputs.su2n_chain_labels(5))
+    _prefix_case(g, 1e-8, 4000, 1023)
 
 
 def test_prefix_random_pair_d64():

@@ -65,6 +65,27 @@ def test_reference_arm_under_torchrun_world2():
 
 
 # ------------------------------------------------- batched sets across ranks
+def test_cost_model_dimension_estimate():
+    """The cost model's dimension is the exact string count for Pauli-string
+    sets (checked against the oracle's integer closure, which shares no code
+    with it) and d^2 - 1 for dense random sets."""
+    import numpy as np
+    import oracle.closure as oc
+    from paper_2506_01120_gb300 import inputs, shard
+    for s in inputs.batched_sets(40, seed=3):
+        est = shard.estimate_dim(s["generators"])
+        if s["kind"] == "pauli":
+            assert est == len(oc.pauli_closure(s["labels"]))
+        else:
+            assert est == s["d"] ** 2 - 1
+    g = inputs.generators_from_labels(inputs.su2n_chain_labels(4))
+    assert shard.estimate_dim(g) == 255
+    assert shard.estimate_dim(3.0 * inputs.generators_from_labels(inputs.so2n_chain_labels(4))) == 28
+    assert shard.pauli_string_bits(np.eye(4) + 0.1) is None
+    # small Pauli closures cost far less than generic sets of the same d
+    assert shard.set_cost(64, 3, dim=30) < 1e-3 * shard.set_cost(64, 3)
+
+
 def test_lpt_assignment_balances_and_covers():
     from paper_2506_01120_gb300 import shard
     costs = [shard.set_cost(d, k) for d, k in [(64, 2), (64, 6), (32, 3), (16, 2), (8, 5), (64, 4), (8, 2)]]
@@ -88,17 +109,23 @@ def _shard_worker(rank, world, port, q):
     dist.init_process_group("gloo")
     sets = [s["generators"] for s in inputs.batched_sets(12, seed=5, dims=(8, 16))]
 
-    def fake_closure(gs, tol, **opts):
-        # stands in for the GPU call: one deterministic number per set
-        return [int(g.shape[1] * 100 + g.shape[0]) for g in gs], [0] * len(gs)
+    def fake_closure(gs, tol, return_basis, **opts):
+        # stands in for the GPU call: one deterministic number (and a small
+        # array standing for the basis) per set
+        dims = [int(g.shape[1] * 100 + g.shape[0]) for g in gs]
+        bases = [np.full((2, 2), float(x)) for x in dims] if return_basis else None
+        return dims, [0] * len(gs), bases
 
     def gather(obj):
         out = [None] * world
         dist.all_gather_object(out, obj)
         return out
 
-    dims, stats = shard.run_sharded(sets, 1e-8, rank, world, fake_closure, gather)
-    q.put((rank, dims, stats))
+    dims, stats, none = shard.run_sharded(sets, 1e-8, rank, world, fake_closure, gather)
+    assert none is None
+    dims_b, stats_b, bases = shard.run_sharded(sets, 1e-8, rank, world, fake_closure, gather, gather_bases=True)
+    assert dims_b == dims and stats_b == stats
+    q.put((rank, dims, stats, [float(b[0, 0]) for b in bases]))
     dist.destroy_process_group()
 
 
@@ -117,5 +144,6 @@ def test_run_sharded_gathers_every_set_gloo():
     res = sorted(q.get(timeout=10) for _ in range(2))
     sets = [s["generators"] for s in inputs.batched_sets(12, seed=5, dims=(8, 16))]
     want = [int(g.shape[1] * 100 + g.shape[0]) for g in sets]
-    for rank, dims, stats in res:
+    for rank, dims, stats, bases in res:
         assert dims == want and stats == [0] * 12
+        assert bases == [float(x) for x in want]          # every rank holds every set's basis
