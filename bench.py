@@ -376,7 +376,9 @@ def config5_leg(stream, window_mixed=2_000_000, window_fp64=20_000):
                                          "eps_screen": r.report["eps_screen"],
                                          "tau_screen": r.report["tau_screen"], "n_gray": r.report["n_gray"],
                                          "min_acc_rel_res": r.report["min_acc_rel_res"],
-                                         "min_acc_screen_rel_res": r.report["min_acc_screen_rel_res"]},
+                                         "min_acc_screen_rel_res": r.report["min_acc_screen_rel_res"],
+                                         "screen_margin": (r.report["min_acc_screen_rel_res"] / r.report["tau_screen"]
+                                                           if prec == "mixed" else None)},
                      "saturated_window": {"candidates": w.report["brackets_checked"], "time_s": tw,
                                           "brackets_per_s": rate, "dim_after": w.dim,
                                           "n_flagged": w.report["n_flagged"]},

@@ -125,7 +125,10 @@ typedef struct {
                                  q = ceil(|V| / 4096).  Default 0 (the report
                                  field is then -1) */
   double screen_kappa;        /* factor of the measured tau_screen; 0 =
-                                 default (10) */
+                                 default (4).  A smaller factor narrows the
+                                 band of true residuals the screen could reject
+                                 and flags more noise for the FP64 recheck
+                                 (time, not correctness) */
 } lc_options;
 
 typedef struct {

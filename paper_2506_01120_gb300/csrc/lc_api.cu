@@ -145,7 +145,7 @@ class Closure {
     Ksat_ = (o.autotune && o.block_k <= 0) ? std::min(K_, mixed_ ? 16384 : 2048) : K_;
     measured_tau_ = mixed_ && !(o.tau_screen > 0);
     tau_ = o.tau_screen > 0 ? o.tau_screen : kTauHi;
-    kappa_ = o.screen_kappa > 0 ? o.screen_kappa : 10.0;
+    kappa_ = o.screen_kappa > 0 ? o.screen_kappa : kKappa;
     // accept iff ||r||^2 > a ||h||^2 + b: relative (a, b) = (tol^2, 0), absolute (0, tol^2)
     tol_rel2_ = o.tol_mode == LC_TOL_ABSOLUTE ? 0.0 : tol * tol;
     tol_abs2_ = o.tol_mode == LC_TOL_ABSOLUTE ? tol * tol : 0.0;
@@ -254,7 +254,14 @@ class Closure {
   static constexpr double kTauLo = 4.76837158203125e-7; // 2^-21, a few FP32 ulps
   static constexpr int kProbeRows = 128, kProbeSingles = 64;
   bool measured_tau_ = false;
-  double kappa_ = 10.0, tau_max_used_ = 0.0;
+  // tau_screen = kKappa * eps: candidates screened above it are rechecked in
+  // FP64 (so a noise flag costs time, never a wrong decision), while a true
+  // residual in (tol, tau] would be rejected by the screen.  The largest
+  // screened residual seen among millions of dependent candidates stays within
+  // ~1.2 eps of the probe's eps, so 4 eps keeps noise flags rare and the band
+  // of possible wrong rejects narrow.
+  static constexpr double kKappa = 4.0;
+  double kappa_ = kKappa, tau_max_used_ = 0.0;
   long long N_probe_ = 0, probes_ = 0, gray_ = 0;
   float* rho2f_ = nullptr;            // screened rho^2 of the flagged candidates, flag order
   // orthonormality check
@@ -286,6 +293,9 @@ class Closure {
   unsigned int* bar_ = nullptr;
   double* ws64_ = nullptr;
   static constexpr size_t kWs64 = size_t(2) << 20;   // split-K workspace, doubles
+  static constexpr size_t kWsK = size_t(8) << 20;    // split-K partials of the projection, floats (32 MB)
+  float* wsk_ = nullptr;
+  int* part_ = nullptr;             // per-chunk counts of the multi-CTA compactions
   DevStats* stats_ = nullptr;
   DevStatus* st_ = nullptr;
   __nv_bfloat16 *Vhi_ = nullptr, *Vlo_ = nullptr, *VThi_ = nullptr, *VTlo_ = nullptr;
@@ -314,6 +324,7 @@ class Closure {
     need_ = ar_.take<int>(1);
     bar_ = ar_.take<unsigned int>(2);
     ws64_ = ar_.take<double>(kWs64);
+    part_ = ar_.take<int>(3 * kCmpCtas);
     if (alg3_) {
       B64_ = ar_.take<double>((size_t)ncap_ * ldp_);
       Hraw_ = ar_.take<double>((size_t)K_ * ldp_);
@@ -342,6 +353,7 @@ class Closure {
       Clo_ = ar_.take<__nv_bfloat16>((size_t)Kpad_ * ldp_);
       hn2c_ = ar_.take<float>(Kpad_);
       rho2f_ = ar_.take<float>(Kpad_);
+      wsk_ = ar_.take<float>(kWsK);
       nz_idx_ = ar_.take<int>(Kpad_);
       nnz_ = ar_.take<int>(1);
       if (tc_bracket_) {
@@ -568,7 +580,9 @@ class Closure {
     if (mixed_) {
       gemm_flops_ += 2.0 * 6.0 * (double)host_->stats.nnonzero * (double)N_ * (double)P_;
       gray_ += host_->stats.ngray;
-      if (measured_tau_) tau_max_used_ = std::max(tau_max_used_, std::sqrt((double)host_->stats.tau2));
+      // (the device clamps in single precision: report the clamped double value)
+      if (measured_tau_)
+        tau_max_used_ = std::max(tau_max_used_, std::min(kTauHi, std::max(kTauLo, std::sqrt((double)host_->stats.tau2))));
     }
     const int f = host_->stats.nflag;
     if (f > 0) {
@@ -593,13 +607,13 @@ class Closure {
     // rest are packed into consecutive rows of S64
     ph_begin();
     LC_TRY(rownorm2_f64(kb, P_, H64_, ldp_, hn2_, s_));
-    LC_TRY(compact_nonzero_f64(hn2_, kb, eta_ * eta_, nz_idx_, nnz_, hn2c64_, s_));
+    LC_TRY(compact_nonzero_f64(hn2_, kb, eta_ * eta_, nz_idx_, nnz_, hn2c64_, s_, part_));
     LC_TRY(cudaMemcpyAsync(&host_->nnz, nnz_, sizeof(int), cudaMemcpyDeviceToHost, s_));
     LC_TRY(cudaStreamSynchronize(s_));
     const int nnz = host_->nnz;
     if (nnz > 0) LC_TRY(gather_rows_f64(H64_, ldp_, nz_idx_, nnz, P_, S64_, ldp_, s_));
     ph_end(PH_SCREEN);
-    launches_ += 4;
+    launches_ += 5;
     if (nnz == 0) {
       nonzero_ += 0;
       return LC_OK;
@@ -616,9 +630,9 @@ class Closure {
     // are dependent
     ph_begin();
     LC_TRY(screen_compact_f64(hn2c64_, rn2_, nnz, eta_ * eta_, 0.25 * tol_rel2_, 0.25 * tol_abs2_, idx_, stats_, s_,
-                              nullptr, nz_idx_));
+                              nullptr, nz_idx_, part_));
     ph_end(PH_SCREEN);
-    launches_ += 4;
+    launches_ += 5;
     return after_screen(t0);
   }
 
@@ -640,7 +654,7 @@ class Closure {
     LC_TRY(probe_eps(hn2c_, rn2f_, S, stats_, (float)kappa_, (float)kTauLo, (float)kTauHi, s_));
     ph_end(PH_SCREEN);
     ++probes_;
-    launches_ += 4;
+    launches_ += 2;     // probe rows and eps; the GEMMs count themselves
     return LC_OK;
   }
 
@@ -693,6 +707,9 @@ class Closure {
     g1.spin_cap = opt.spin_cap;
     g1.st = st_;
     g1.cfg = gemm_cfg_;
+    g1.ws = wsk_;
+    g1.ws_floats = kWsK;
+    g1.launches = &launches_;
     ph_begin();
     cudaError_t e = split_gemm_tcgen05(g1, s_);
     if (e != cudaSuccess) return e;
@@ -717,6 +734,7 @@ class Closure {
     g2.spin_cap = opt.spin_cap;
     g2.st = st_;
     g2.cfg = gemm_cfg_;
+    g2.launches = &launches_;
     e = cudaMemsetAsync(rn2f_, 0, sizeof(float) * M, s_);
     if (e != cudaSuccess) return e;
     ph_begin();
@@ -748,15 +766,15 @@ class Closure {
     const float es = (float)eta_screen_, ts = (float)tau_;
     ph_begin();
     // (B is not normalised: for Algorithm 3 the floor scales with ||B_l|| ||B_m||)
-    LC_TRY(compact_nonzero(hn2f_, kb, es * es, nz_idx_, nnz_, s_, alg3_ ? bn2_ : nullptr, t0));
+    LC_TRY(compact_nonzero(hn2f_, kb, es * es, nz_idx_, nnz_, s_, alg3_ ? bn2_ : nullptr, t0, part_));
     LC_TRY(gather_candidates(Hhi_, Hlo_, ldp_, hn2f_, nz_idx_, nnz_, kb, ldp_, Chi_, Clo_, hn2c_, s_));
     ph_end(PH_SCREEN);
     LC_TRY(screen_gemms(kb));
     ph_begin();
     LC_TRY(screen_compact_f32(hn2c_, rn2f_, kb, es * es, ts * ts, idx_, stats_, s_, nnz_, nz_idx_,
-                              measured_tau_ ? 1 : 0, rho2f_));
+                              measured_tau_ ? 1 : 0, rho2f_, part_));
     ph_end(PH_SCREEN);
-    launches_ += 6;
+    launches_ += 6;     // bracket, compaction (2), gather, screen (2); the GEMMs count themselves
     return after_screen(t0);
   }
 
@@ -1012,7 +1030,7 @@ void lc_default_options(lc_options* o) {
   o->precision = LC_PREC_MIXED_BF16X3;
   o->eta_abs = 1e-12;
   o->tau_screen = 0.0;          // measured
-  o->screen_kappa = 10.0;
+  o->screen_kappa = 4.0;
   o->tol_mode = LC_TOL_RELATIVE;
   o->autotune = 0;
   o->ortho_check = 0;

@@ -355,6 +355,104 @@ __global__ void __launch_bounds__(1024) k_screen_compact(const T* __restrict__ h
   }
 }
 
+// Multi-CTA ordered compaction (two launches).  The candidates are cut into
+// kCmpCtas contiguous chunks; pass 1 counts each chunk's flags (and its
+// statistics) into part[], pass 2 writes each chunk's flagged positions at
+// the offset given by the counts of the chunks before it, so the output order
+// is candidate order, as the single-CTA kernel produces.
+template <typename T>
+__device__ __forceinline__ int screen_flag(const T* hn2, const T* rn2, int c, T eta2, T tau2, T tau2_abs) {
+  const T h = hn2[c], r = rn2[c];
+  return (h > eta2 && r > tau2 * h + tau2_abs) ? 1 : 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCmpThreads) k_screen_pass1(const T* __restrict__ hn2, const T* __restrict__ rn2,
+                                                           int count, T eta2, T tau2, T tau2_abs, DevStats* stats,
+                                                           const int* __restrict__ count_dev, int measured,
+                                                           int* __restrict__ part) {
+  __shared__ int sf[kCmpThreads / 32], sn[kCmpThreads / 32], sg[kCmpThreads / 32];
+  __shared__ double sm[kCmpThreads / 32];
+  if (count_dev) count = min(count, *count_dev);
+  if (measured) tau2 = (T)stats->tau2;
+  const double eps2 = measured ? (double)stats->eps2 : -1.0;
+  const int chunk = (count + gridDim.x - 1) / gridDim.x;
+  const int c0 = blockIdx.x * chunk, c1 = min(count, c0 + chunk);
+  int nf = 0, nz = 0, gray = 0;
+  double rej = 0.0;
+  for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+    const T h = hn2[c], r = rn2[c];
+    const int f = screen_flag(hn2, rn2, c, eta2, tau2, tau2_abs);
+    nf += f;
+    if (h > eta2) {
+      ++nz;
+      if (!f) {
+        rej = fmax(rej, sqrt((double)r / (double)h));
+        if (eps2 >= 0.0 && (double)r > eps2 * (double)h) ++gray;
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    nf += __shfl_xor_sync(0xffffffffu, nf, o);
+    nz += __shfl_xor_sync(0xffffffffu, nz, o);
+    gray += __shfl_xor_sync(0xffffffffu, gray, o);
+    rej = fmax(rej, __shfl_xor_sync(0xffffffffu, rej, o));
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) { sf[w] = nf; sn[w] = nz; sg[w] = gray; sm[w] = rej; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int a = 0, b = 0, g = 0;
+    double m = 0.0;
+    for (int i = 0; i < kCmpThreads / 32; ++i) { a += sf[i]; b += sn[i]; g += sg[i]; m = fmax(m, sm[i]); }
+    part[blockIdx.x] = a;
+    part[kCmpCtas + blockIdx.x] = b;
+    part[2 * kCmpCtas + blockIdx.x] = g;
+    if (m > 0.0) atomicMax(&stats->max_screen_rej_bits, dbits(m));
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCmpThreads) k_screen_pass2(const T* __restrict__ hn2, const T* __restrict__ rn2,
+                                                           int count, T eta2, T tau2, T tau2_abs,
+                                                           int* __restrict__ idx, DevStats* stats,
+                                                           const int* __restrict__ count_dev,
+                                                           const int* __restrict__ map, int measured,
+                                                           float* __restrict__ rho2_flag,
+                                                           const int* __restrict__ part) {
+  __shared__ int wsum[kCmpThreads / 32];
+  __shared__ int base;
+  if (count_dev) count = min(count, *count_dev);
+  if (measured) tau2 = (T)stats->tau2;
+  const int chunk = (count + gridDim.x - 1) / gridDim.x;
+  const int c0 = blockIdx.x * chunk, c1 = min(count, c0 + chunk);
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int b = 0; b < (int)blockIdx.x; ++b) o += part[b];
+    base = o;
+    if (blockIdx.x == 0) {
+      int a = 0, z = 0, g = 0;
+      for (int b = 0; b < (int)gridDim.x; ++b) { a += part[b]; z += part[kCmpCtas + b]; g += part[2 * kCmpCtas + b]; }
+      stats->nflag = a;
+      stats->nnonzero = z;
+      stats->ngray = g;
+    }
+  }
+  __syncthreads();
+  for (int t0 = c0; t0 < c1; t0 += blockDim.x) {
+    const int c = t0 + threadIdx.x;
+    const int f = c < c1 ? screen_flag(hn2, rn2, c, eta2, tau2, tau2_abs) : 0;
+    int tot;
+    const int at = base + cta_excl_scan(f, &tot, wsum);
+    if (f) {
+      idx[at] = map ? map[c] : c;
+      if (rho2_flag) rho2_flag[at] = (float)((double)rn2[c] / (double)hn2[c]);
+    }
+    if (threadIdx.x == 0) base += tot;
+    __syncthreads();
+  }
+}
+
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The
 // wait is bounded: after limit_ns the CTA records LC_ERR_TIMEOUT and returns
 // false, and the caller leaves the kernel.
@@ -536,6 +634,57 @@ __global__ void k_defect_max(const double* __restrict__ G, int rows, int cols, i
   if ((threadIdx.x & 31) == 0) atomicMax(out_bits, dbits(m));
 }
 
+// two-pass forms of k_compact_nonzero_f64 (see cta_excl_scan)
+__global__ void __launch_bounds__(kCmpThreads) k_nonzero_f64_pass1(const double* __restrict__ hn2, int count,
+                                                                double eta2, int* __restrict__ part) {
+  __shared__ int sw[kCmpThreads / 32];
+  const int chunk = (count + gridDim.x - 1) / gridDim.x;
+  const int c0 = blockIdx.x * chunk, c1 = min(count, c0 + chunk);
+  int n = 0;
+  for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) n += hn2[c] > eta2 ? 1 : 0;
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = n;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int i = 0; i < kCmpThreads / 32; ++i) t += sw[i];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kCmpThreads) k_nonzero_f64_pass2(const double* __restrict__ hn2, int count,
+                                                                double eta2, int* __restrict__ nz_idx,
+                                                                int* __restrict__ nnz, double* __restrict__ hn2c,
+                                                                const int* __restrict__ part) {
+  __shared__ int wsum[kCmpThreads / 32];
+  __shared__ int base;
+  const int chunk = (count + gridDim.x - 1) / gridDim.x;
+  const int c0 = blockIdx.x * chunk, c1 = min(count, c0 + chunk);
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int b = 0; b < (int)blockIdx.x; ++b) o += part[b];
+    base = o;
+    if (blockIdx.x == 0) {
+      int t = 0;
+      for (int b = 0; b < (int)gridDim.x; ++b) t += part[b];
+      *nnz = t;
+    }
+  }
+  __syncthreads();
+  for (int t0 = c0; t0 < c1; t0 += blockDim.x) {
+    const int c = t0 + threadIdx.x;
+    const int f = (c < c1 && hn2[c] > eta2) ? 1 : 0;
+    int tot;
+    const int at = base + cta_excl_scan(f, &tot, wsum);
+    if (f) {
+      nz_idx[at] = c;
+      hn2c[at] = hn2[c];
+    }
+    if (threadIdx.x == 0) base += tot;
+    __syncthreads();
+  }
+}
+
 __global__ void k_zero_stats(DevStats* stats, int ncur) {
   stats->ncur = ncur;
   stats->naccepted = 0;
@@ -650,7 +799,14 @@ cudaError_t gather_rows_f64(const double* src, int lds, const int* idx, int coun
 
 cudaError_t screen_compact_f64(const double* hn2, const double* rn2, int count, double eta2, double tau2,
                                double tau2_abs, int* idx, DevStats* stats, cudaStream_t s, const int* count_dev,
-                               const int* map) {
+                               const int* map, int* part) {
+  if (part) {
+    k_screen_pass1<double><<<kCmpCtas, kCmpThreads, 0, s>>>(hn2, rn2, count, eta2, tau2, tau2_abs, stats, count_dev,
+                                                            0, part);
+    k_screen_pass2<double><<<kCmpCtas, kCmpThreads, 0, s>>>(hn2, rn2, count, eta2, tau2, tau2_abs, idx, stats,
+                                                            count_dev, map, 0, nullptr, part);
+    return cudaGetLastError();
+  }
   k_screen_compact<double><<<1, 1024, 0, s>>>(hn2, rn2, count, eta2, tau2, tau2_abs, idx, stats, count_dev, map, 0,
                                               nullptr);
   return cudaGetLastError();
@@ -658,7 +814,14 @@ cudaError_t screen_compact_f64(const double* hn2, const double* rn2, int count, 
 
 cudaError_t screen_compact_f32(const float* hn2, const float* rn2, int count, float eta2, float tau2, int* idx,
                                DevStats* stats, cudaStream_t s, const int* count_dev, const int* map, int measured,
-                               float* rho2_flag) {
+                               float* rho2_flag, int* part) {
+  if (part) {
+    k_screen_pass1<float><<<kCmpCtas, kCmpThreads, 0, s>>>(hn2, rn2, count, eta2, tau2, 0.f, stats, count_dev,
+                                                           measured, part);
+    k_screen_pass2<float><<<kCmpCtas, kCmpThreads, 0, s>>>(hn2, rn2, count, eta2, tau2, 0.f, idx, stats, count_dev,
+                                                           map, measured, rho2_flag, part);
+    return cudaGetLastError();
+  }
   k_screen_compact<float><<<1, 1024, 0, s>>>(hn2, rn2, count, eta2, tau2, 0.f, idx, stats, count_dev, map,
                                              measured, rho2_flag);
   return cudaGetLastError();
@@ -700,7 +863,12 @@ cudaError_t need_pass2(int f, const double* hn2, const double* rn2, double eta2,
 }
 
 cudaError_t compact_nonzero_f64(const double* hn2, int count, double eta2, int* nz_idx, int* nnz, double* hn2c,
-                                cudaStream_t s) {
+                                cudaStream_t s, int* part) {
+  if (part) {
+    k_nonzero_f64_pass1<<<kCmpCtas, kCmpThreads, 0, s>>>(hn2, count, eta2, part);
+    k_nonzero_f64_pass2<<<kCmpCtas, kCmpThreads, 0, s>>>(hn2, count, eta2, nz_idx, nnz, hn2c, part);
+    return cudaGetLastError();
+  }
   k_compact_nonzero_f64<<<1, 1024, 0, s>>>(hn2, count, eta2, nz_idx, nnz, hn2c);
   return cudaGetLastError();
 }

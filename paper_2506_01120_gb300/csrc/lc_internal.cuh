@@ -105,6 +105,33 @@ inline int device_sm_count() {
   return cache[dev];
 }
 
+// Multi-CTA ordered compaction: kCmpCtas contiguous chunks, kCmpThreads
+// threads per CTA; part[] holds per-chunk counts between the two passes.
+constexpr int kCmpCtas = 64;
+constexpr int kCmpThreads = 256;
+
+// exclusive prefix of f over the CTA (kCmpThreads threads), *total = the CTA's sum
+__device__ __forceinline__ int cta_excl_scan(int f, int* total, int* wsum) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned mask = __ballot_sync(0xffffffffu, f);
+  const int pre = __popc(mask & ((1u << lane) - 1u));
+  if (lane == 0) wsum[w] = __popc(mask);
+  __syncthreads();
+  if (w == 0) {
+    int v = lane < kCmpThreads / 32 ? wsum[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int n = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += n;
+    }
+    if (lane < kCmpThreads / 32) wsum[lane] = v;          // inclusive
+  }
+  __syncthreads();
+  const int r = (w ? wsum[w - 1] : 0) + pre;
+  *total = wsum[kCmpThreads / 32 - 1];
+  __syncthreads();
+  return r;
+}
+
 // ------------------------------------------------------------ FP64 kernels
 // (lc_fp64.cu)
 cudaError_t pack_generators(const double2* g, int k, int d, int ldp, double* out,
@@ -142,12 +169,15 @@ cudaError_t gather_rows_f64(const double* src, int lds, const int* idx, int coun
                             double* dst, int ldd, cudaStream_t s);
 // flags candidates with hn2 > eta^2 and rn2 > tau^2 hn2 + tau2_abs; writes the
 // flagged candidate positions in order to idx and their count to stats->nflag
+// part (optional, >= 3 * 64 ints of device scratch): use the multi-CTA
+// two-pass form instead of one CTA
 cudaError_t screen_compact_f64(const double* hn2, const double* rn2, int count, double eta2,
                                double tau2, double tau2_abs, int* idx, DevStats* stats, cudaStream_t s,
-                               const int* count_dev = nullptr, const int* map = nullptr);
-// ordered indices of the candidates with hn2 > eta2, their count (*nnz) and norms
+                               const int* count_dev = nullptr, const int* map = nullptr, int* part = nullptr);
+// ordered indices of the candidates with hn2 > eta2, their count (*nnz) and
+// norms (part: optional scratch of kCmpCtas ints for the multi-CTA form)
 cudaError_t compact_nonzero_f64(const double* hn2, int count, double eta2, int* nz_idx, int* nnz,
-                                double* hn2c, cudaStream_t s);
+                                double* hn2c, cudaStream_t s, int* part = nullptr);
 // count_dev (optional): live count on the device; map (optional): idx[i] = map[position];
 // measured != 0: tau^2 is stats->tau2 (the probe's threshold) and screen rejects
 // with rho^2 > stats->eps2 are counted in stats->ngray; rho2_flag (optional)
@@ -155,7 +185,7 @@ cudaError_t compact_nonzero_f64(const double* hn2, int count, double eta2, int* 
 cudaError_t screen_compact_f32(const float* hn2, const float* rn2, int count, float eta2,
                                float tau2, int* idx, DevStats* stats, cudaStream_t s,
                                const int* count_dev = nullptr, const int* map = nullptr, int measured = 0,
-                               float* rho2_flag = nullptr);
+                               float* rho2_flag = nullptr, int* part = nullptr);
 cudaError_t zero_stats(DevStats* stats, int ncur, cudaStream_t s);
 
 // ------------------------------------------------------ mixed-precision path
@@ -198,7 +228,7 @@ cudaError_t bracket_q64(const __nv_bfloat16* Qhi, const __nv_bfloat16* Qlo, long
 // (bn2, optional: squared norms of the bracket operands' rows; the floor is
 // then eta2 * bn2[l] * bn2[m] for the pair t0 + position)
 cudaError_t compact_nonzero(const float* hn2, int count, float eta2, int* nz_idx, int* nnz, cudaStream_t s,
-                            const double* bn2 = nullptr, long long t0 = 0);
+                            const double* bn2 = nullptr, long long t0 = 0, int* part = nullptr);
 // rows nz_idx[0 .. *nnz) of H (and their norms) -> consecutive rows of C
 cudaError_t gather_candidates(const __nv_bfloat16* Hhi, const __nv_bfloat16* Hlo, int ldh, const float* hn2,
                               const int* nz_idx, const int* nnz, int count, int ncols, __nv_bfloat16* Chi,
@@ -237,6 +267,11 @@ struct SplitGemmArgs {
   long long spin_cap;
   DevStatus* st;
   int cfg;                         // tile configuration, 0 .. split_gemm_num_cfgs() - 1
+  // optional FP32 workspace for a split-K projection (epilogue 0 with fewer
+  // output tiles than SMs); null = no split
+  float* ws;
+  size_t ws_floats;
+  long long* launches;             // optional: incremented by the kernels launched
 };
 cudaError_t split_gemm_tcgen05(const SplitGemmArgs& a, cudaStream_t s);
 // tile extents of split_gemm_tcgen05: with N a multiple of split_gemm_tile_n(),

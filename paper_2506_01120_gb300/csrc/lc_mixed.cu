@@ -270,6 +270,65 @@ __global__ void __launch_bounds__(1024) k_compact_nonzero(const float* __restric
   if (threadIdx.x == 0) *nnz = base;
 }
 
+__device__ __forceinline__ int nonzero_flag(const float* hn2, int c, float eta2, const double* bn2, long long t0) {
+  float floor2 = eta2;
+  if (bn2) {
+    int l, m;
+    pair_from_index(t0 + c, &l, &m);
+    floor2 = (float)((double)eta2 * bn2[l] * bn2[m]);
+  }
+  return hn2[c] > floor2 ? 1 : 0;
+}
+
+// two-pass forms of k_compact_nonzero (see cta_excl_scan)
+__global__ void __launch_bounds__(kCmpThreads) k_nonzero_pass1(const float* __restrict__ hn2, int count, float eta2,
+                                                            const double* __restrict__ bn2, long long t0,
+                                                            int* __restrict__ part) {
+  __shared__ int sw[kCmpThreads / 32];
+  const int chunk = (count + gridDim.x - 1) / gridDim.x;
+  const int c0 = blockIdx.x * chunk, c1 = min(count, c0 + chunk);
+  int n = 0;
+  for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) n += nonzero_flag(hn2, c, eta2, bn2, t0);
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = n;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int i = 0; i < kCmpThreads / 32; ++i) t += sw[i];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kCmpThreads) k_nonzero_pass2(const float* __restrict__ hn2, int count, float eta2,
+                                                            const double* __restrict__ bn2, long long t0,
+                                                            int* __restrict__ nz_idx, int* __restrict__ nnz,
+                                                            const int* __restrict__ part) {
+  __shared__ int wsum[kCmpThreads / 32];
+  __shared__ int base;
+  const int chunk = (count + gridDim.x - 1) / gridDim.x;
+  const int c0 = blockIdx.x * chunk, c1 = min(count, c0 + chunk);
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int b = 0; b < (int)blockIdx.x; ++b) o += part[b];
+    base = o;
+    if (blockIdx.x == 0) {
+      int t = 0;
+      for (int b = 0; b < (int)gridDim.x; ++b) t += part[b];
+      *nnz = t;
+    }
+  }
+  __syncthreads();
+  for (int tt = c0; tt < c1; tt += blockDim.x) {
+    const int c = tt + threadIdx.x;
+    const int f = c < c1 ? nonzero_flag(hn2, c, eta2, bn2, t0) : 0;
+    int tot;
+    const int at = base + cta_excl_scan(f, &tot, wsum);
+    if (f) nz_idx[at] = c;
+    if (threadIdx.x == 0) base += tot;
+    __syncthreads();
+  }
+}
+
 // row i of the compacted block <- row nz_idx[i] (16-byte vectors)
 __global__ void k_gather_candidates(const __nv_bfloat16* __restrict__ Hhi, const __nv_bfloat16* __restrict__ Hlo,
                                     int ldh, const float* __restrict__ hn2, const int* __restrict__ nz_idx,
@@ -312,7 +371,12 @@ cudaError_t build_q(const double* V, int ldv, int r0, int r1, int d, __nv_bfloat
 }
 
 cudaError_t compact_nonzero(const float* hn2, int count, float eta2, int* nz_idx, int* nnz, cudaStream_t s,
-                            const double* bn2, long long t0) {
+                            const double* bn2, long long t0, int* part) {
+  if (part) {
+    k_nonzero_pass1<<<kCmpCtas, kCmpThreads, 0, s>>>(hn2, count, eta2, bn2, t0, part);
+    k_nonzero_pass2<<<kCmpCtas, kCmpThreads, 0, s>>>(hn2, count, eta2, bn2, t0, nz_idx, nnz, part);
+    return cudaGetLastError();
+  }
   k_compact_nonzero<<<1, 1024, 0, s>>>(hn2, count, eta2, nz_idx, nnz, bn2, t0);
   return cudaGetLastError();
 }

@@ -204,6 +204,8 @@ struct GemmParams {
   int epilogue;
   uint64_t limit_ns;
   DevStatus* st;
+  int ksplit, kchunk;     // K split into ksplit ranges of kchunk k-slices (epilogue 3)
+  float* Wpart;           // epilogue 3: FP32 partial tile of split s at Wpart[s][row][col] (row stride N)
 };
 
 template <class G>
@@ -227,13 +229,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   // and both operands are reused from L2 instead of re-read from DRAM.
   constexpr int GROUP_M = 8;
   const int ntn = p.N / BN, ntm = p.M / BM;
-  const int id = blockIdx.x;
+  // split-K (epilogue 3): CTA blockIdx.x covers tile id of k-range split
+  const int split = blockIdx.x / (ntn * ntm);
+  const int id = blockIdx.x - split * (ntn * ntm);
   const int per_group = GROUP_M * ntn;
   const int g = id / per_group, first_m = g * GROUP_M;
   const int gm = min(GROUP_M, ntm - first_m);
   const int in_g = id - g * per_group;
   const int m0 = (first_m + in_g % gm) * BM, n0 = (in_g / gm) * BN;
-  const int nk = p.K / BK;
+  const int kt_begin = p.epilogue == 3 ? split * p.kchunk : 0;
+  const int nk = p.epilogue == 3 ? min(p.kchunk, p.K / BK - kt_begin) : p.K / BK;
   if (p.Mdev && m0 >= *p.Mdev) return;      // whole CTA: rows past the live count
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
 
@@ -272,7 +277,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (*(volatile int*)&abort_flag) break;
       uint8_t* st = smem + s * STAGE_BYTES;
       mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-      const int kx = kt * BK;
+      const int kx = (kt_begin + kt) * BK;
       tma_load_2d(st, &mAhi, &full_bar[s], kx, m0);
       tma_load_2d(st + TILE_A_BYTES, &mAlo, &full_bar[s], kx, m0);
       tma_load_2d(st + 2 * TILE_A_BYTES, &mBhi, &full_bar[s], kx, n0);
@@ -367,7 +372,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
           }
         } else {
-          float4* o = reinterpret_cast<float4*>(p.Df32 + (long long)row * p.ldd + col);
+          float* base = p.epilogue == 3 ? p.Wpart + ((long long)split * p.M + row) * p.N + col
+                                        : p.Df32 + (long long)row * p.ldd + col;
+          float4* o = reinterpret_cast<float4*>(base);
 #pragma unroll
           for (int i = 0; i < 8; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
         }
@@ -431,6 +438,24 @@ bool tcgen05_available() {
 }
 
 namespace {
+// Sum of the split-K partials in split order (deterministic), stored as the
+// split BF16 pair of epilogue 0; rows of tiles the GEMM skipped (at or past
+// the live count) are skipped here too.
+__global__ void k_splitk_reduce_bf16(const float* __restrict__ W, int S, int M, int N, const int* __restrict__ Mdev,
+                                     __nv_bfloat16* __restrict__ Dhi, __nv_bfloat16* __restrict__ Dlo, int ldd) {
+  const int rows = Mdev ? min(M, (*Mdev + BM - 1) / BM * BM) : M;
+  const long long tot = (long long)rows * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / N), c = (int)(e % N);
+    float v = 0.f;
+    for (int q = 0; q < S; ++q) v += W[((long long)q * M + r) * N + c];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    Dhi[(long long)r * ldd + c] = h;
+    Dlo[(long long)r * ldd + c] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
 template <class G>
 cudaError_t split_gemm_cfg(const SplitGemmArgs& a, cudaStream_t s) {
   if (a.M <= 0 || a.N <= 0) return cudaSuccess;
@@ -458,8 +483,36 @@ cudaError_t split_gemm_cfg(const SplitGemmArgs& a, cudaStream_t s) {
   p.epilogue = a.epilogue;
   p.limit_ns = a.spin_cap > 0 ? (uint64_t)a.spin_cap : 4000000000ull;
   p.st = a.st;
+  p.ksplit = 1;
+  p.kchunk = a.K / G::BK;
+  p.Wpart = nullptr;
   const int ntiles = (a.N / G::BN) * (a.M / BM);
+  // Split-K for the projection when its output has fewer tiles than there are
+  // SMs (few basis rows, long rows: large d): every split keeps >= 4 k-slices
+  // and all splits are non-empty; the partials are summed in order.
+  const int nkt = a.K / G::BK, sms = device_sm_count();
+  if (a.epilogue == 0 && a.ws && ntiles < sms && nkt >= 8) {
+    int S = std::min((sms + ntiles - 1) / ntiles, nkt / 4);
+    S = (int)std::min<long long>(S, (long long)(a.ws_floats / ((size_t)a.M * a.N)));
+    if (S > 1) {
+      const int kchunk = (nkt + S - 1) / S;
+      S = (nkt + kchunk - 1) / kchunk;
+      p.epilogue = 3;
+      p.ksplit = S;
+      p.kchunk = kchunk;
+      p.Wpart = a.ws;
+      k_split_gemm<G><<<ntiles * S, NTHREADS, G::SMEM, s>>>(mAhi, mAlo, mBhi, mBlo, p);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      const long long tot = (long long)a.M * a.N;
+      const int grid = (int)std::min<long long>((tot + 255) / 256, (long long)sms * 8);
+      k_splitk_reduce_bf16<<<grid, 256, 0, s>>>(a.ws, S, a.M, a.N, a.Mdev, a.Dhi, a.Dlo, a.ldd);
+      if (a.launches) *a.launches += 2;
+      return cudaGetLastError();
+    }
+  }
   k_split_gemm<G><<<ntiles, NTHREADS, G::SMEM, s>>>(mAhi, mAlo, mBhi, mBlo, p);
+  if (a.launches) *a.launches += 1;
   return cudaGetLastError();
 }
 }  // namespace
@@ -870,11 +923,12 @@ extern "C" LC_API int lc_split_gemm_f32_noalloc(const float* A, const float* B, 
 // 128 rows of X, the full M = 128 instruction shape.
 // Persistent CTAs: CTA c takes a contiguous share of the block's pairs in
 // pair order, so consecutive units mostly keep l and Y stays in shared
-// memory (a new l reloads it).  Warp 0 streams Y and X with TMA and negates
-// the -Ai half of Y in shared memory; warp 1 issues a unit's 24 MMAs into one
-// of two TMEM accumulators; warps 2-5 copy an accumulator into a padded
-// shared tile T (row r = TMEM lane r) and write packed row j of each bracket
-// from row j and column j of D:
+// memory (a new l reloads it).  Warp 0 streams Y and X with TMA (X through a
+// two-stage ring, so the next unit's operands load during this unit's MMAs)
+// and negates the -Ai half of Y in shared memory; warp 1 issues a unit's 24
+// MMAs into one of two TMEM accumulators; warps 2-5 copy one pair's
+// accumulator rows into a padded shared tile T and write packed row j of its
+// bracket from row j and column j of D:
 //   S[j][k] = s2 (Im D[j][k] + Im D[k][j])   (k > j)
 //   S[j][j] = s1 2 Im D[j][j]
 //   S[j][k] = s2 (Re D[j][k] - Re D[k][j])   (k < j)
@@ -889,10 +943,11 @@ constexpr int Q_D = 64;
 constexpr int QP_TILE = 128 * 64 * 2;     // one 128-row x 64-column BF16 tile (16 KB)
 constexpr int QP_HALF = QP_TILE / 2;      // 64 rows (8 KB): one TMA box
 constexpr int QP_Y = 4 * QP_TILE;         // Y0hi, Y0lo, Y1hi, Y1lo
-constexpr int QP_X = 4 * QP_TILE;         // X0hi, X0lo, X1hi, X1lo  (X0 = Br, X1 = Bi)
+constexpr int QP_X = 4 * QP_TILE;         // one X stage: X0hi, X0lo, X1hi, X1lo  (X0 = Br, X1 = Bi)
+constexpr int QP_XSTAGES = 2;             // X ring: the next unit's operands load during this unit's MMAs
 constexpr int QP_TLD = 129;               // padded row stride of T (floats): conflict-free rows and columns
-constexpr int QP_T = 128 * QP_TLD * 4;
-constexpr int QP_SMEM = QP_Y + QP_X + QP_T + 1024;
+constexpr int QP_T = 64 * QP_TLD * 4;     // one pair's D at a time
+constexpr int QP_SMEM = QP_Y + QP_XSTAGES * QP_X + QP_T + 1024;
 constexpr int QP_TMEM = 256;              // two 128-column accumulators
 constexpr int QP_THREADS = 192;
 
@@ -937,7 +992,7 @@ __global__ void __launch_bounds__(QP_THREADS, 1)
                   int count, __nv_bfloat16* __restrict__ Hhi, __nv_bfloat16* __restrict__ Hlo, int ldh,
                   float* __restrict__ hn2, uint64_t limit_ns, DevStatus* st) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t x_full, x_empty, y_full, y_ready, done_bar;
+  __shared__ __align__(8) uint64_t x_full[QP_XSTAGES], x_empty[QP_XSTAGES], y_full, y_ready, done_bar;
   __shared__ __align__(8) uint64_t t_full[2], t_empty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag, epi_abort;
@@ -947,11 +1002,13 @@ __global__ void __launch_bounds__(QP_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* Y = smem;
-  uint8_t* X = smem + QP_Y;
-  float* T = reinterpret_cast<float*>(smem + QP_Y + QP_X);
+  uint8_t* X = smem + QP_Y;                                 // stage s at X + s * QP_X
+  float* T = reinterpret_cast<float*>(smem + QP_Y + QP_XSTAGES * QP_X);
   if (threadIdx.x == 0) {
-    mbar_init(&x_full, 1);
-    mbar_init(&x_empty, 1);
+    for (int q = 0; q < QP_XSTAGES; ++q) {
+      mbar_init(&x_full[q], 1);
+      mbar_init(&x_empty[q], 1);
+    }
     mbar_init(&y_full, 1);
     mbar_init(&y_ready, 1);
     mbar_init(&done_bar, 1);
@@ -984,11 +1041,22 @@ __global__ void __launch_bounds__(QP_THREADS, 1)
     int cur_l = -1, ny = 0, nx = 0;
     while (w.more()) {
       const int n = w.size();
-      // the single X stage (and Y) is free once the previous unit's MMAs retired
-      if (nx > 0 && !wait_or_abort(&x_empty, (uint32_t)(nx - 1) & 1u, limit_ns, ab)) {
+      const int xs = nx % QP_XSTAGES;
+      // stage xs is free once the MMAs of unit nx - QP_XSTAGES retired
+      if (nx >= QP_XSTAGES &&
+          !wait_or_abort(&x_empty[xs], (uint32_t)(nx / QP_XSTAGES - 1) & 1u, limit_ns, ab)) {
         if (lane == 0) record_timeout(st, SITE_GEMM_TMA_WAIT, nx);
         *ab = 1;
         break;
+      }
+      // Y may be replaced once every MMA that reads it (up to unit nx - 1) retired
+      if (w.l != cur_l && nx > 0) {
+        const int ps = (nx - 1) % QP_XSTAGES;
+        if (!wait_or_abort(&x_empty[ps], (uint32_t)((nx - 1) / QP_XSTAGES) & 1u, limit_ns, ab)) {
+          if (lane == 0) record_timeout(st, SITE_GEMM_TMA_WAIT, -nx);
+          *ab = 1;
+          break;
+        }
       }
       if (w.l != cur_l) {
         if (lane == 0) {
@@ -1023,13 +1091,14 @@ __global__ void __launch_bounds__(QP_THREADS, 1)
         cur_l = w.l;
       }
       if (lane == 0) {
-        mbar_expect_tx(&x_full, n * 4 * QP_HALF);
+        uint8_t* Xs = X + xs * QP_X;
+        mbar_expect_tx(&x_full[xs], n * 4 * QP_HALF);
         for (int q = 0; q < n; ++q) {
           const int rr = (w.m + q) * 2 * Q_D, rI = rr + Q_D;
-          tma_load_2d(X + 0 * QP_TILE + q * QP_HALF, &mQhi, &x_full, 0, rr);
-          tma_load_2d(X + 1 * QP_TILE + q * QP_HALF, &mQlo, &x_full, 0, rr);
-          tma_load_2d(X + 2 * QP_TILE + q * QP_HALF, &mQhi, &x_full, 0, rI);
-          tma_load_2d(X + 3 * QP_TILE + q * QP_HALF, &mQlo, &x_full, 0, rI);
+          tma_load_2d(Xs + 0 * QP_TILE + q * QP_HALF, &mQhi, &x_full[xs], 0, rr);
+          tma_load_2d(Xs + 1 * QP_TILE + q * QP_HALF, &mQlo, &x_full[xs], 0, rr);
+          tma_load_2d(Xs + 2 * QP_TILE + q * QP_HALF, &mQhi, &x_full[xs], 0, rI);
+          tma_load_2d(Xs + 3 * QP_TILE + q * QP_HALF, &mQlo, &x_full[xs], 0, rI);
         }
       }
       __syncwarp();
@@ -1037,7 +1106,8 @@ __global__ void __launch_bounds__(QP_THREADS, 1)
       w.next(n);
     }
     // drain: no copy may still be writing shared memory when the CTA leaves
-    if (nx > 0) mbar_wait_bounded(&x_full, (uint32_t)(nx - 1) & 1u, kDrainNs);
+    for (int k = (nx > QP_XSTAGES ? nx - QP_XSTAGES : 0); k < nx; ++k)
+      mbar_wait_bounded(&x_full[k % QP_XSTAGES], (uint32_t)(k / QP_XSTAGES) & 1u, kDrainNs);
     if (ny > 0) mbar_wait_bounded(&y_full, (uint32_t)(ny - 1) & 1u, kDrainNs);
   } else if (warp == 1) {
     // ---------------- MMA issuer
@@ -1049,7 +1119,8 @@ __global__ void __launch_bounds__(QP_THREADS, 1)
       while (w.more()) {
         const int n = w.size();
         const int b = u & 1;
-        bool ok = wait_or_abort(&x_full, (uint32_t)u & 1u, limit_ns, ab);
+        const int xs = u % QP_XSTAGES;
+        bool ok = wait_or_abort(&x_full[xs], (uint32_t)(u / QP_XSTAGES) & 1u, limit_ns, ab);
         if (ok && w.l != cur_l) {
           ok = wait_or_abort(&y_ready, (uint32_t)ny & 1u, limit_ns, ab);
           ++ny;
@@ -1065,7 +1136,7 @@ __global__ void __launch_bounds__(QP_THREADS, 1)
         const uint32_t d = tmem + (uint32_t)(b * 128);
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          const uint32_t xh = smem_u32(X + (2 * c) * QP_TILE), xl = xh + QP_TILE;
+          const uint32_t xh = smem_u32(X + xs * QP_X + (2 * c) * QP_TILE), xl = xh + QP_TILE;
           const uint32_t yh = smem_u32(Y + (2 * c) * QP_TILE), yl = yh + QP_TILE;
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
@@ -1077,7 +1148,7 @@ __global__ void __launch_bounds__(QP_THREADS, 1)
             mma_bf16(d, dxl, dyh, idesc, 1u);
           }
         }
-        mma_commit(&x_empty);        // X (and Y) may be overwritten once these retire
+        mma_commit(&x_empty[xs]);    // X stage xs (and Y) may be overwritten once these retire
         mma_commit(&t_full[b]);      // accumulator b complete
         ++u;
         w.next(n);
@@ -1085,10 +1156,13 @@ __global__ void __launch_bounds__(QP_THREADS, 1)
       mma_commit(&done_bar);         // every issued MMA has retired when this arrives
     }
   } else {
-    // ---------------- epilogue: warps 2-5, TMEM lane quarter q = warp % 4
+    // ---------------- epilogue: warps 2-5, TMEM lane quarter q = warp % 4.
+    // T holds one pair's D at a time: the two warps whose TMEM lanes carry the
+    // pair copy its 64 rows in, then all four warps write its packed rows
+    // (thread t: row t % 64, columns 32 (t / 64) .. + 31).
     const int q = warp & 3;
-    const int r = q * 32 + lane;                 // accumulator row: pair r / 64, row j = r % 64
-    const int p = r >> 6, j = r & 63;
+    const int et = threadIdx.x - 64;             // 0 .. 127
+    const int jr = et & 63, kh = (et >> 6) * 32;
     const float s1 = rsqrtf((float)Q_D), s2 = sqrtf(2.f / (float)Q_D);
     UnitWalk w;
     w.start(tb, te);
@@ -1100,47 +1174,47 @@ __global__ void __launch_bounds__(QP_THREADS, 1)
       named_bar_sync(1, 128);
       if (*(volatile int*)&epi_abort) break;     // uniform: only written before this barrier
       tc_fence_after();
-      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 128);
-      float* Tr = T + r * QP_TLD;
+      for (int p = 0; p < n; ++p) {
+        if ((q >> 1) == p) {                      // warp-uniform: lanes 64 p .. 64 p + 63
+          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 128);
+          float* Tr = T + ((q & 1) * 32 + lane) * QP_TLD;
 #pragma unroll 1
-      for (int c = 0; c < 128; c += 32) {
-        float v[32];
-        tmem_ld_32cols(taddr + (uint32_t)c, v);
+          for (int c = 0; c < 128; c += 32) {
+            float v[32];
+            tmem_ld_32cols(taddr + (uint32_t)c, v);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) Tr[c + i] = v[i];
-      }
-      tc_fence_before();
-      named_bar_sync(1, 128);                    // T complete; accumulator b free
-      if (threadIdx.x == 64) mbar_arrive(&t_empty[b]);
-      if (p < n) {
+            for (int i = 0; i < 32; ++i) Tr[c + i] = v[i];
+          }
+        }
+        if (p == n - 1) tc_fence_before();
+        named_bar_sync(1, 128);                  // this pair's D is in T
+        if (p == n - 1 && threadIdx.x == 64) mbar_arrive(&t_empty[b]);   // accumulator b free
         const long long pidx = w.t + p - t0;     // position of the pair in the block
-        const float* Tc = T + (p * 64) * QP_TLD + j;   // column j of this pair's D
-        __nv_bfloat16* oh = Hhi + pidx * ldh + (long long)j * Q_D;
-        __nv_bfloat16* ol = Hlo + pidx * ldh + (long long)j * Q_D;
+        const float* Tr = T + jr * QP_TLD;       // row jr of D
+        const float* Tc = T + jr;                // column jr of D: Tc[k * QP_TLD]
+        __nv_bfloat16* oh = Hhi + pidx * ldh + (long long)jr * Q_D + kh;
+        __nv_bfloat16* ol = Hlo + pidx * ldh + (long long)jr * Q_D + kh;
         float ss = 0.f;
-#pragma unroll 1
-        for (int c = 0; c < Q_D; c += 32) {
-          __align__(16) __nv_bfloat16 hi[32], lo[32];
+        __align__(16) __nv_bfloat16 hi[32], lo[32];
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const int k = c + i;
-            const float re_jk = Tr[k], im_jk = Tr[Q_D + k];
-            const float re_kj = Tc[k * QP_TLD], im_kj = Tc[k * QP_TLD + Q_D];
-            const float v = (k > j) ? s2 * (im_jk + im_kj) : ((k == j) ? s1 * (im_jk + im_kj) : s2 * (re_jk - re_kj));
-            ss = fmaf(v, v, ss);
-            hi[i] = __float2bfloat16_rn(v);
-            lo[i] = __float2bfloat16_rn(v - __bfloat162float(hi[i]));
-          }
+        for (int i = 0; i < 32; ++i) {
+          const int k = kh + i;
+          const float re_jk = Tr[k], im_jk = Tr[Q_D + k];
+          const float re_kj = Tc[k * QP_TLD], im_kj = Tc[k * QP_TLD + Q_D];
+          const float v = (k > jr) ? s2 * (im_jk + im_kj) : ((k == jr) ? s1 * (im_jk + im_kj) : s2 * (re_jk - re_kj));
+          ss = fmaf(v, v, ss);
+          hi[i] = __float2bfloat16_rn(v);
+          lo[i] = __float2bfloat16_rn(v - __bfloat162float(hi[i]));
+        }
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            reinterpret_cast<uint4*>(oh + c)[i] = reinterpret_cast<const uint4*>(hi)[i];
-            reinterpret_cast<uint4*>(ol + c)[i] = reinterpret_cast<const uint4*>(lo)[i];
-          }
+        for (int i = 0; i < 4; ++i) {
+          reinterpret_cast<uint4*>(oh)[i] = reinterpret_cast<const uint4*>(hi)[i];
+          reinterpret_cast<uint4*>(ol)[i] = reinterpret_cast<const uint4*>(lo)[i];
         }
         for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
         if (lane == 0) atomicAdd(&hn2[pidx], ss);
+        named_bar_sync(1, 128);                  // T may be overwritten
       }
-      named_bar_sync(1, 128);                    // T may be overwritten by the next unit
       ++u;
       w.next(n);
     }

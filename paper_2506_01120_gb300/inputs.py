@@ -184,6 +184,30 @@ def batched_sets(nsets: int = 256, seed: int = 1120, dims=(8, 16, 32, 64)):
     return sets
 
 
+def random_subalgebra_set(kind: str, d: int, k: int, seed: int) -> np.ndarray:
+    """k seeded random generators inside a proper subalgebra of su(d), unit
+    Frobenius norm:
+      "so"    -- real antisymmetric matrices (i.i.d. N(0, 1) above the
+                 diagonal), which are anti-Hermitian and span so(d);
+      "block" -- block-diagonal diag(a, b) of two independent random traceless
+                 anti-Hermitian (d/2) x (d/2) blocks, inside su(d/2) + su(d/2)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(k):
+        if kind == "so":
+            x = np.triu(rng.standard_normal((d, d)), 1)
+            a = (x - x.T).astype(np.complex128)
+        elif kind == "block":
+            h = d // 2
+            a = np.zeros((d, d), dtype=np.complex128)
+            a[:h, :h] = random_antihermitian(h, rng, unit_frobenius=False)
+            a[h:, h:] = random_antihermitian(h, rng, unit_frobenius=False)
+        else:
+            raise ValueError(kind)
+        out.append(a / np.sqrt(np.sum(np.abs(a) ** 2)))
+    return np.stack(out)
+
+
 def random_set(d: int, k: int, seed: int, traceless: bool = True) -> np.ndarray:
     """k seeded random anti-Hermitian generators of size d (unit Frobenius norm)."""
     rng = np.random.default_rng(seed)

@@ -44,3 +44,17 @@ def test_tfim_ops():
     assert [l for l, _ in xs] == ["XIII", "IXII", "IIXI", "IIIX"]
     assert [l for l, _ in zz] == ["ZZII", "IZZI", "IIZZ"]
     assert all(c == 1.0 for _, c in xs + zz)
+
+
+def test_random_subalgebra_sets_have_the_stated_structure():
+    import numpy as np
+    from paper_2506_01120_gb300 import inputs
+    g = inputs.random_subalgebra_set("so", 8, 3, seed=1)
+    assert g.shape == (3, 8, 8)
+    assert np.all(g.imag == 0) and np.allclose(g, -np.transpose(g, (0, 2, 1)))
+    b = inputs.random_subalgebra_set("block", 8, 2, seed=2)
+    assert np.all(b[:, :4, 4:] == 0) and np.all(b[:, 4:, :4] == 0)
+    for a in b:
+        np.testing.assert_allclose(a, -a.conj().T, atol=1e-15)
+        assert abs(np.trace(a[:4, :4])) < 1e-14 and abs(np.trace(a[4:, 4:])) < 1e-14
+    assert np.allclose([np.sum(np.abs(a) ** 2) for a in np.concatenate([g, b])], 1.0)
