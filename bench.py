@@ -66,6 +66,11 @@ def parse():
     ap.add_argument("--batched-full", action="store_true",
                     help="batched leg: full Algorithm 4 sweep per set instead of the saturation exit")
     ap.add_argument("--autotune", type=int, default=0, help="lc_options.autotune for the timed steps")
+    ap.add_argument("--legs-only", action="store_true",
+                    help="run only the --legs workload legs and print them as one line")
+    ap.add_argument("--kernel-case", action="store_true",
+                    help="run only the profiling case: the saturated su(64) state (all 4095 Pauli strings) resumed "
+                         "at the pair (3000, 0) for 31,744 candidates, i.e. blocks of 1024 .. 16384 pairs")
     return ap.parse_args()
 
 
@@ -433,6 +438,20 @@ def batched_leg(full: bool):
             "brackets_per_s": cand / t, "all_ok": ok, "all_dims_exact": exact}
 
 
+def kernel_case():
+    """A short, fixed launch sequence for ncu: the su(64) basis made of the 4095
+    non-identity Pauli strings (orthonormal, saturated) resumed at the pair
+    (3000, 0) for 31,744 candidates, so the sweep runs blocks of 1024, 2048,
+    4096, 8192 and 16384 pairs (the last one the saturated-phase size)."""
+    from paper_2506_01120_gb300 import binding, inputs
+    n = 6
+    labels = ["".join("IXYZ"[(s >> (2 * q)) & 3] for q in range(n)) for s in range(1, 4 ** n)]
+    V = inputs.generators_from_labels(labels)
+    r = binding.lie_closure_resume(V, (3000, 0), 1e-8, precision="mixed", max_candidates=31744, profile=1)
+    return {"kernel_case": {"dim": r.dim, "candidates": r.report["brackets_checked"],
+                            "phase_s": r.report["t_phase_s"], "version": binding.version()}}
+
+
 def next_rows_leg():
     """Algorithm 3 on the su(64) chain (mixed, host API), Algorithm 2 against
     Algorithm 4 in FP64 (full sweeps), and an su(64) closure stopped halfway
@@ -492,6 +511,22 @@ def run_ours(args, world, rank, local, pg):
     if args.next_rows:
         if rank == 0:
             print(json.dumps({"next_rows": next_rows_leg()}), flush=True)
+        return
+    if args.kernel_case:
+        if rank == 0:
+            print(json.dumps(kernel_case()), flush=True)
+        return
+    if args.legs_only:
+        legs = set(x for x in args.legs.split(",") if x and x != "none")
+        out = {}
+        if "config5" in legs:
+            out["su128_random2_d128"] = config5_leg(torch.cuda.current_stream())
+        if "config3" in legs:
+            out["so20_chain_d1024"] = config3_leg(torch.cuda.current_stream())
+        if "batched" in legs:
+            out["batched256_d8to64"] = batched_leg(args.batched_full)
+        if rank == 0:
+            print(json.dumps({"workloads": out}), flush=True)
         return
     if args.pauli_only:
         peaks, peak_src = measured_peaks()

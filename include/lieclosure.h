@@ -89,7 +89,7 @@ typedef struct {
                                  growing; 0 = automatic (16384 mixed, 2048 FP64,
                                  capped by an 8 GB buffer budget) */
   int block_k_growth;         /* candidates per block while the basis grows;
-                                 0 = automatic (1024) */
+                                 0 = automatic (1024; 256 when d >= 256) */
   int saturation_exit;        /* nonzero: stop once |V| reaches the largest
                                  possible dimension (d^2 - 1, plus one if a
                                  generator has a trace); not in the paper,
@@ -125,7 +125,7 @@ typedef struct {
                                  q = ceil(|V| / 4096).  Default 0 (the report
                                  field is then -1) */
   double screen_kappa;        /* factor of the measured tau_screen; 0 =
-                                 default (4).  A smaller factor narrows the
+                                 default (10).  A smaller factor narrows the
                                  band of true residuals the screen could reject
                                  and flags more noise for the FP64 recheck
                                  (time, not correctness) */

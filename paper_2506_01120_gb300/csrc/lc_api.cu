@@ -139,7 +139,10 @@ class Closure {
     K = std::max(K, k_);         // the generator pass is one block
     K_ = std::max(1, K);
     Kpad_ = round_up(K_, 128);
-    Kgrow_ = std::min(K_, o.block_k_growth > 0 ? o.block_k_growth : 1024);
+    // growth blocks: 1024 candidates; 256 for large d (P >= 2^16), where each
+    // flagged candidate costs an FP64 bracket of 8 d^3 flop and smaller blocks
+    // flag fewer in-block duplicates
+    Kgrow_ = std::min(K_, o.block_k_growth > 0 ? o.block_k_growth : (P_ >= (1 << 16) ? 256 : 1024));
     // saturated-phase block: the allocated K_, except that an autotuned call
     // without an explicit block_k starts from the fixed default
     Ksat_ = (o.autotune && o.block_k <= 0) ? std::min(K_, mixed_ ? 16384 : 2048) : K_;
@@ -256,11 +259,13 @@ class Closure {
   bool measured_tau_ = false;
   // tau_screen = kKappa * eps: candidates screened above it are rechecked in
   // FP64 (so a noise flag costs time, never a wrong decision), while a true
-  // residual in (tol, tau] would be rejected by the screen.  The largest
-  // screened residual seen among millions of dependent candidates stays within
-  // ~1.2 eps of the probe's eps, so 4 eps keeps noise flags rare and the band
-  // of possible wrong rejects narrow.
-  static constexpr double kKappa = 4.0;
+  // residual in (tol, tau] would be rejected by the screen.  The probe rows
+  // carry no bracket rounding, so a bracket's screened noise runs above the
+  // probe's eps: the largest screened residual among millions of dependent
+  // brackets measured up to 2.2 eps (random d = 64 pair), and at 4 eps the
+  // su(128) chain's noise flags tripled its run time.  10 eps keeps noise
+  // flags rare.
+  static constexpr double kKappa = 10.0;
   double kappa_ = kKappa, tau_max_used_ = 0.0;
   long long N_probe_ = 0, probes_ = 0, gray_ = 0;
   float* rho2f_ = nullptr;            // screened rho^2 of the flagged candidates, flag order
@@ -1030,7 +1035,7 @@ void lc_default_options(lc_options* o) {
   o->precision = LC_PREC_MIXED_BF16X3;
   o->eta_abs = 1e-12;
   o->tau_screen = 0.0;          // measured
-  o->screen_kappa = 4.0;
+  o->screen_kappa = 10.0;
   o->tol_mode = LC_TOL_RELATIVE;
   o->autotune = 0;
   o->ortho_check = 0;
@@ -1058,7 +1063,7 @@ const char* lc_status_string(int s) {
   }
 }
 
-const char* lc_version(void) { return "lieclosure-gb300 0.3 (sm_103a; screening GEMM 128x256x32)"; }
+const char* lc_version(void) { return "lieclosure-gb300 0.4 (sm_103a; screening GEMM 128x256x32, split-K; d = 64 bracket M = 128 persistent)"; }
 
 int lie_closure_dev(const lc_c128* generators, int k, int d, double tol, lc_c128* basis_out, long long* dim_out,
                     long long max_dim, const lc_options* opt, lc_report* rep, void* stream) {

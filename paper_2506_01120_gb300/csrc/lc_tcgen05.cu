@@ -917,18 +917,18 @@ extern "C" LC_API int lc_split_gemm_f32_noalloc(const float* A, const float* B, 
 // [V_l, V_m] = [iA, iB] = -(AB - BA) = D - D^dagger.  With the tcgen05 product
 // MMA(X, Y) = X Y^T and Hr^T = Hr, Hi^T = -Hi:
 //   Re D = MMA(Br, Ar) + MMA(Bi, Ai),   Im D = -MMA(Br, Ai) + MMA(Bi, Ar),
-// one accumulator of 128 columns [Re D | Im D] from two 64-wide k-chunks:
-//   chunk 0: X = Br, Y = [Ar; -Ai];   chunk 1: X = Bi, Y = [Ai; Ar].
-// Two pairs (l, m), (l, m + 1) share A and so Y: their B operands fill the
-// 128 rows of X, the full M = 128 instruction shape.
+// four N = 64 products into one 128-column accumulator [Re D | Im D] (the
+// minus sign by the instruction's negate-A bit).  Two pairs (l, m), (l, m + 1)
+// share A: their B operands fill the 128 rows of X, the full M = 128 shape.
 // Persistent CTAs: CTA c takes a contiguous share of the block's pairs in
-// pair order, so consecutive units mostly keep l and Y stays in shared
-// memory (a new l reloads it).  Warp 0 streams Y and X with TMA (X through a
-// two-stage ring, so the next unit's operands load during this unit's MMAs)
-// and negates the -Ai half of Y in shared memory; warp 1 issues a unit's 24
-// MMAs into one of two TMEM accumulators; warps 2-5 copy one pair's
-// accumulator rows into a padded shared tile T and write packed row j of its
-// bracket from row j and column j of D:
+// pair order, so consecutive units mostly keep l and A's tiles (Ar, Ai, split
+// hi/lo, 32 KB) stay in shared memory; a new l reloads them.  Warp 0 streams A
+// and B with TMA (B through a two-stage ring, so the next unit's operands load
+// during this unit's MMAs); warp 1 issues a unit's 48 MMAs into one of two
+// TMEM accumulators; warps 2-9 drain an accumulator: each thread holds half of
+// one accumulator row (its Re and Im columns) in registers, writes it to a
+// padded shared tile T, and after a barrier reads column j of D from T to
+// write half of packed row j of the bracket:
 //   S[j][k] = s2 (Im D[j][k] + Im D[k][j])   (k > j)
 //   S[j][j] = s1 2 Im D[j][j]
 //   S[j][k] = s2 (Re D[j][k] - Re D[k][j])   (k < j)
@@ -940,16 +940,17 @@ namespace lc {
 namespace {
 
 constexpr int Q_D = 64;
-constexpr int QP_TILE = 128 * 64 * 2;     // one 128-row x 64-column BF16 tile (16 KB)
-constexpr int QP_HALF = QP_TILE / 2;      // 64 rows (8 KB): one TMA box
-constexpr int QP_Y = 4 * QP_TILE;         // Y0hi, Y0lo, Y1hi, Y1lo
-constexpr int QP_X = 4 * QP_TILE;         // one X stage: X0hi, X0lo, X1hi, X1lo  (X0 = Br, X1 = Bi)
-constexpr int QP_XSTAGES = 2;             // X ring: the next unit's operands load during this unit's MMAs
+constexpr int QP_BOX = 64 * 64 * 2;       // one 64-row x 64-column BF16 tile (8 KB): one TMA box
+constexpr int QP_Y = 4 * QP_BOX;          // Ar hi, Ar lo, Ai hi, Ai lo
+constexpr int QP_XT = 2 * QP_BOX;         // one 128-row X tile (two pairs' 64-row boxes)
+constexpr int QP_X = 4 * QP_XT;           // one X stage: Br hi, Br lo, Bi hi, Bi lo
+constexpr int QP_XSTAGES = 2;
 constexpr int QP_TLD = 129;               // padded row stride of T (floats): conflict-free rows and columns
-constexpr int QP_T = 64 * QP_TLD * 4;     // one pair's D at a time
+constexpr int QP_T = 128 * QP_TLD * 4;    // both pairs' D
 constexpr int QP_SMEM = QP_Y + QP_XSTAGES * QP_X + QP_T + 1024;
 constexpr int QP_TMEM = 256;              // two 128-column accumulators
-constexpr int QP_THREADS = 192;
+constexpr int QP_EPI_WARPS = 8;
+constexpr int QP_THREADS = 64 + 32 * QP_EPI_WARPS;
 
 // Bounded wait that also gives up as soon as another role has aborted.
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, uint64_t limit_ns,
@@ -992,7 +993,7 @@ __global__ void __launch_bounds__(QP_THREADS, 1)
                   int count, __nv_bfloat16* __restrict__ Hhi, __nv_bfloat16* __restrict__ Hlo, int ldh,
                   float* __restrict__ hn2, uint64_t limit_ns, DevStatus* st) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t x_full[QP_XSTAGES], x_empty[QP_XSTAGES], y_full, y_ready, done_bar;
+  __shared__ __align__(8) uint64_t x_full[QP_XSTAGES], x_empty[QP_XSTAGES], y_full, done_bar;
   __shared__ __align__(8) uint64_t t_full[2], t_empty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag, epi_abort;
@@ -1001,7 +1002,7 @@ __global__ void __launch_bounds__(QP_THREADS, 1)
   if (p0 >= p1) return;                                   // whole CTA: no pairs
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* Y = smem;
+  uint8_t* Y = smem;                                        // Ar hi, Ar lo, Ai hi, Ai lo
   uint8_t* X = smem + QP_Y;                                 // stage s at X + s * QP_X
   float* T = reinterpret_cast<float*>(smem + QP_Y + QP_XSTAGES * QP_X);
   if (threadIdx.x == 0) {
@@ -1010,7 +1011,6 @@ __global__ void __launch_bounds__(QP_THREADS, 1)
       mbar_init(&x_empty[q], 1);
     }
     mbar_init(&y_full, 1);
-    mbar_init(&y_ready, 1);
     mbar_init(&done_bar, 1);
     for (int b = 0; b < 2; ++b) {
       mbar_init(&t_full[b], 1);
@@ -1035,84 +1035,60 @@ __global__ void __launch_bounds__(QP_THREADS, 1)
   const long long tb = t0 + p0, te = t0 + p1;
 
   if (warp == 0) {
-    // ---------------- producer: Y per new l (then negate -Ai), X per unit
-    UnitWalk w;
-    w.start(tb, te);
-    int cur_l = -1, ny = 0, nx = 0;
-    while (w.more()) {
-      const int n = w.size();
-      const int xs = nx % QP_XSTAGES;
-      // stage xs is free once the MMAs of unit nx - QP_XSTAGES retired
-      if (nx >= QP_XSTAGES &&
-          !wait_or_abort(&x_empty[xs], (uint32_t)(nx / QP_XSTAGES - 1) & 1u, limit_ns, ab)) {
-        if (lane == 0) record_timeout(st, SITE_GEMM_TMA_WAIT, nx);
-        *ab = 1;
-        break;
-      }
-      // Y may be replaced once every MMA that reads it (up to unit nx - 1) retired
-      if (w.l != cur_l && nx > 0) {
-        const int ps = (nx - 1) % QP_XSTAGES;
-        if (!wait_or_abort(&x_empty[ps], (uint32_t)((nx - 1) / QP_XSTAGES) & 1u, limit_ns, ab)) {
-          if (lane == 0) record_timeout(st, SITE_GEMM_TMA_WAIT, -nx);
+    // ---------------- producer (lane 0): A's tiles per new l, B's per unit
+    if (lane == 0) {
+      UnitWalk w;
+      w.start(tb, te);
+      int cur_l = -1, ny = 0, nx = 0;
+      while (w.more()) {
+        const int n = w.size();
+        const int xs = nx % QP_XSTAGES;
+        // stage xs is free once the MMAs of unit nx - QP_XSTAGES retired
+        if (nx >= QP_XSTAGES &&
+            !wait_or_abort(&x_empty[xs], (uint32_t)(nx / QP_XSTAGES - 1) & 1u, limit_ns, ab)) {
+          record_timeout(st, SITE_GEMM_TMA_WAIT, nx);
           *ab = 1;
           break;
         }
-      }
-      if (w.l != cur_l) {
-        if (lane == 0) {
+        if (w.l != cur_l) {
+          // A's tiles may be replaced once every MMA reading them (up to unit nx - 1) retired
+          if (nx > 0 && !wait_or_abort(&x_empty[(nx - 1) % QP_XSTAGES], (uint32_t)((nx - 1) / QP_XSTAGES) & 1u,
+                                       limit_ns, ab)) {
+            record_timeout(st, SITE_GEMM_TMA_WAIT, -nx);
+            *ab = 1;
+            break;
+          }
           const int ra = w.l * 2 * Q_D, ri = ra + Q_D;
           mbar_expect_tx(&y_full, QP_Y);
-          tma_load_2d(Y + 0 * QP_TILE, &mQhi, &y_full, 0, ra);
-          tma_load_2d(Y + 0 * QP_TILE + QP_HALF, &mQhi, &y_full, 0, ri);
-          tma_load_2d(Y + 1 * QP_TILE, &mQlo, &y_full, 0, ra);
-          tma_load_2d(Y + 1 * QP_TILE + QP_HALF, &mQlo, &y_full, 0, ri);
-          tma_load_2d(Y + 2 * QP_TILE, &mQhi, &y_full, 0, ri);
-          tma_load_2d(Y + 2 * QP_TILE + QP_HALF, &mQhi, &y_full, 0, ra);
-          tma_load_2d(Y + 3 * QP_TILE, &mQlo, &y_full, 0, ri);
-          tma_load_2d(Y + 3 * QP_TILE + QP_HALF, &mQlo, &y_full, 0, ra);
+          tma_load_2d(Y + 0 * QP_BOX, &mQhi, &y_full, 0, ra);
+          tma_load_2d(Y + 1 * QP_BOX, &mQlo, &y_full, 0, ra);
+          tma_load_2d(Y + 2 * QP_BOX, &mQhi, &y_full, 0, ri);
+          tma_load_2d(Y + 3 * QP_BOX, &mQlo, &y_full, 0, ri);
+          ++ny;
+          cur_l = w.l;
         }
-        __syncwarp();
-        ++ny;
-        if (!wait_or_abort(&y_full, (uint32_t)(ny - 1) & 1u, limit_ns, ab)) {
-          if (lane == 0) record_timeout(st, SITE_GEMM_TMA_WAIT, -ny);
-          *ab = 1;
-          break;
-        }
-        // Y0 = [Ar; -Ai]: flip the sign bits of the lower half (hi and lo)
-        uint32_t* w0 = reinterpret_cast<uint32_t*>(Y + QP_HALF);
-        uint32_t* w1 = reinterpret_cast<uint32_t*>(Y + QP_TILE + QP_HALF);
-        for (int i = lane; i < QP_HALF / 4; i += 32) {
-          w0[i] ^= 0x80008000u;
-          w1[i] ^= 0x80008000u;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor core
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&y_ready);
-        cur_l = w.l;
-      }
-      if (lane == 0) {
         uint8_t* Xs = X + xs * QP_X;
-        mbar_expect_tx(&x_full[xs], n * 4 * QP_HALF);
+        mbar_expect_tx(&x_full[xs], n * 4 * QP_BOX);
         for (int q = 0; q < n; ++q) {
           const int rr = (w.m + q) * 2 * Q_D, rI = rr + Q_D;
-          tma_load_2d(Xs + 0 * QP_TILE + q * QP_HALF, &mQhi, &x_full[xs], 0, rr);
-          tma_load_2d(Xs + 1 * QP_TILE + q * QP_HALF, &mQlo, &x_full[xs], 0, rr);
-          tma_load_2d(Xs + 2 * QP_TILE + q * QP_HALF, &mQhi, &x_full[xs], 0, rI);
-          tma_load_2d(Xs + 3 * QP_TILE + q * QP_HALF, &mQlo, &x_full[xs], 0, rI);
+          tma_load_2d(Xs + 0 * QP_XT + q * QP_BOX, &mQhi, &x_full[xs], 0, rr);
+          tma_load_2d(Xs + 1 * QP_XT + q * QP_BOX, &mQlo, &x_full[xs], 0, rr);
+          tma_load_2d(Xs + 2 * QP_XT + q * QP_BOX, &mQhi, &x_full[xs], 0, rI);
+          tma_load_2d(Xs + 3 * QP_XT + q * QP_BOX, &mQlo, &x_full[xs], 0, rI);
         }
+        ++nx;
+        w.next(n);
       }
-      __syncwarp();
-      ++nx;
-      w.next(n);
+      // drain: no copy may still be writing shared memory when the CTA leaves
+      for (int k = (nx > QP_XSTAGES ? nx - QP_XSTAGES : 0); k < nx; ++k)
+        mbar_wait_bounded(&x_full[k % QP_XSTAGES], (uint32_t)(k / QP_XSTAGES) & 1u, kDrainNs);
+      if (ny > 0) mbar_wait_bounded(&y_full, (uint32_t)(ny - 1) & 1u, kDrainNs);
     }
-    // drain: no copy may still be writing shared memory when the CTA leaves
-    for (int k = (nx > QP_XSTAGES ? nx - QP_XSTAGES : 0); k < nx; ++k)
-      mbar_wait_bounded(&x_full[k % QP_XSTAGES], (uint32_t)(k / QP_XSTAGES) & 1u, kDrainNs);
-    if (ny > 0) mbar_wait_bounded(&y_full, (uint32_t)(ny - 1) & 1u, kDrainNs);
   } else if (warp == 1) {
-    // ---------------- MMA issuer
+    // ---------------- MMA issuer (lane 0)
     if (lane == 0) {
-      constexpr uint32_t idesc = make_idesc_bf16(128, 128);
+      constexpr uint32_t idesc = make_idesc_bf16(128, 64);
+      constexpr uint32_t idesc_neg = idesc | (1u << 13);        // negate A
       UnitWalk w;
       w.start(tb, te);
       int cur_l = -1, ny = 0, u = 0;
@@ -1122,7 +1098,7 @@ __global__ void __launch_bounds__(QP_THREADS, 1)
         const int xs = u % QP_XSTAGES;
         bool ok = wait_or_abort(&x_full[xs], (uint32_t)(u / QP_XSTAGES) & 1u, limit_ns, ab);
         if (ok && w.l != cur_l) {
-          ok = wait_or_abort(&y_ready, (uint32_t)ny & 1u, limit_ns, ab);
+          ok = wait_or_abort(&y_full, (uint32_t)ny & 1u, limit_ns, ab);
           ++ny;
           cur_l = w.l;
         }
@@ -1134,21 +1110,25 @@ __global__ void __launch_bounds__(QP_THREADS, 1)
         }
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(b * 128);
+        const uint32_t xb = smem_u32(X + xs * QP_X), yb = smem_u32(Y);
+        // (X tile, Y tile, accumulator column offset, negate): the four N = 64 products
+        const uint32_t XT[4] = {xb, xb, xb + 2 * QP_XT, xb + 2 * QP_XT};            // Br, Br, Bi, Bi (hi)
+        const uint32_t YT[4] = {yb, yb + 2 * QP_BOX, yb + 2 * QP_BOX, yb};          // Ar, Ai, Ai, Ar (hi)
+        const uint32_t CO[4] = {0, 64, 0, 64};
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const uint32_t xh = smem_u32(X + xs * QP_X + (2 * c) * QP_TILE), xl = xh + QP_TILE;
-          const uint32_t yh = smem_u32(Y + (2 * c) * QP_TILE), yl = yh + QP_TILE;
+        for (int t = 0; t < 4; ++t) {
+          const uint32_t dsc = (t == 1) ? idesc_neg : idesc;
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             const uint32_t off = kk * 32;
-            const uint64_t dxh = make_sw128_desc(xh + off), dxl = make_sw128_desc(xl + off);
-            const uint64_t dyh = make_sw128_desc(yh + off), dyl = make_sw128_desc(yl + off);
-            mma_bf16(d, dxh, dyh, idesc, (c | kk) ? 1u : 0u);
-            mma_bf16(d, dxh, dyl, idesc, 1u);
-            mma_bf16(d, dxl, dyh, idesc, 1u);
+            const uint64_t xh = make_sw128_desc(XT[t] + off), xl = make_sw128_desc(XT[t] + QP_XT + off);
+            const uint64_t yh = make_sw128_desc(YT[t] + off), yl = make_sw128_desc(YT[t] + QP_BOX + off);
+            mma_bf16(d + CO[t], xh, yh, dsc, (t >= 2 || kk) ? 1u : 0u);   // t = 0, 1 start their columns
+            mma_bf16(d + CO[t], xh, yl, dsc, 1u);
+            mma_bf16(d + CO[t], xl, yh, dsc, 1u);
           }
         }
-        mma_commit(&x_empty[xs]);    // X stage xs (and Y) may be overwritten once these retire
+        mma_commit(&x_empty[xs]);    // X stage xs (and A's tiles) may be overwritten once these retire
         mma_commit(&t_full[b]);      // accumulator b complete
         ++u;
         w.next(n);
@@ -1156,13 +1136,13 @@ __global__ void __launch_bounds__(QP_THREADS, 1)
       mma_commit(&done_bar);         // every issued MMA has retired when this arrives
     }
   } else {
-    // ---------------- epilogue: warps 2-5, TMEM lane quarter q = warp % 4.
-    // T holds one pair's D at a time: the two warps whose TMEM lanes carry the
-    // pair copy its 64 rows in, then all four warps write its packed rows
-    // (thread t: row t % 64, columns 32 (t / 64) .. + 31).
-    const int q = warp & 3;
-    const int et = threadIdx.x - 64;             // 0 .. 127
-    const int jr = et & 63, kh = (et >> 6) * 32;
+    // ---------------- epilogue: warps 2-9.  Warp w reads TMEM lane quarter
+    // q = w % 4 (rows r = 32 q + lane: pair r / 64, row j = r % 64) and column
+    // half h = (w - 2) / 4: Re D[j][32h .. 32h+31] and Im D[j][same].
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const int r = q * 32 + lane;
+    const int p = r >> 6, j = r & 63;
+    const int nthr = 32 * QP_EPI_WARPS;
     const float s1 = rsqrtf((float)Q_D), s2 = sqrtf(2.f / (float)Q_D);
     UnitWalk w;
     w.start(tb, te);
@@ -1171,41 +1151,38 @@ __global__ void __launch_bounds__(QP_THREADS, 1)
       const int n = w.size();
       const int b = u & 1;
       if (!wait_or_abort(&t_full[b], (uint32_t)(u >> 1) & 1u, limit_ns, ab)) epi_abort = 1;
-      named_bar_sync(1, 128);
+      named_bar_sync(1, nthr);
       if (*(volatile int*)&epi_abort) break;     // uniform: only written before this barrier
       tc_fence_after();
-      for (int p = 0; p < n; ++p) {
-        if ((q >> 1) == p) {                      // warp-uniform: lanes 64 p .. 64 p + 63
-          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 128);
-          float* Tr = T + ((q & 1) * 32 + lane) * QP_TLD;
-#pragma unroll 1
-          for (int c = 0; c < 128; c += 32) {
-            float v[32];
-            tmem_ld_32cols(taddr + (uint32_t)c, v);
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 128 + 32 * h);
+      float re[32], im[32];
+      tmem_ld_32cols(taddr, re);
+      tmem_ld_32cols(taddr + 64u, im);
+      float* Tr = T + r * QP_TLD + 32 * h;
 #pragma unroll
-            for (int i = 0; i < 32; ++i) Tr[c + i] = v[i];
-          }
-        }
-        if (p == n - 1) tc_fence_before();
-        named_bar_sync(1, 128);                  // this pair's D is in T
-        if (p == n - 1 && threadIdx.x == 64) mbar_arrive(&t_empty[b]);   // accumulator b free
+      for (int i = 0; i < 32; ++i) {
+        Tr[i] = re[i];
+        Tr[Q_D + i] = im[i];
+      }
+      tc_fence_before();
+      named_bar_sync(1, nthr);                   // T complete; accumulator b free
+      if (threadIdx.x == 64) mbar_arrive(&t_empty[b]);
+      if (p < n) {
         const long long pidx = w.t + p - t0;     // position of the pair in the block
-        const float* Tr = T + jr * QP_TLD;       // row jr of D
-        const float* Tc = T + jr;                // column jr of D: Tc[k * QP_TLD]
-        __nv_bfloat16* oh = Hhi + pidx * ldh + (long long)jr * Q_D + kh;
-        __nv_bfloat16* ol = Hlo + pidx * ldh + (long long)jr * Q_D + kh;
-        float ss = 0.f;
+        const float* Tc = T + (p * 64 + 32 * h) * QP_TLD + j;   // column j of this pair's D, rows 32h ..
         __align__(16) __nv_bfloat16 hi[32], lo[32];
+        float ss = 0.f;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-          const int k = kh + i;
-          const float re_jk = Tr[k], im_jk = Tr[Q_D + k];
-          const float re_kj = Tc[k * QP_TLD], im_kj = Tc[k * QP_TLD + Q_D];
-          const float v = (k > jr) ? s2 * (im_jk + im_kj) : ((k == jr) ? s1 * (im_jk + im_kj) : s2 * (re_jk - re_kj));
+          const int k = 32 * h + i;
+          const float re_kj = Tc[i * QP_TLD], im_kj = Tc[i * QP_TLD + Q_D];
+          const float v = (k > j) ? s2 * (im[i] + im_kj) : ((k == j) ? s1 * (im[i] + im_kj) : s2 * (re[i] - re_kj));
           ss = fmaf(v, v, ss);
           hi[i] = __float2bfloat16_rn(v);
           lo[i] = __float2bfloat16_rn(v - __bfloat162float(hi[i]));
         }
+        __nv_bfloat16* oh = Hhi + pidx * ldh + (long long)j * Q_D + 32 * h;
+        __nv_bfloat16* ol = Hlo + pidx * ldh + (long long)j * Q_D + 32 * h;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           reinterpret_cast<uint4*>(oh)[i] = reinterpret_cast<const uint4*>(hi)[i];
@@ -1213,8 +1190,8 @@ __global__ void __launch_bounds__(QP_THREADS, 1)
         }
         for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
         if (lane == 0) atomicAdd(&hn2[pidx], ss);
-        named_bar_sync(1, 128);                  // T may be overwritten
       }
+      named_bar_sync(1, nthr);                   // T may be overwritten by the next unit
       ++u;
       w.next(n);
     }

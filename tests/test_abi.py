@@ -45,7 +45,7 @@ def test_host_only_calls(built_lib):
     o = binding.make_options("fp64")
     assert o.precision == binding.LC_PREC_FP64
     assert o.eta_abs == 1e-12 and o.tau_screen == 0.0 and o.saturation_exit == 0
-    assert o.screen_kappa == 4.0 and o.tol_mode == binding.LC_TOL_RELATIVE
+    assert o.screen_kappa == 10.0 and o.tol_mode == binding.LC_TOL_RELATIVE
     assert o.autotune == 0 and o.ortho_check == 0
     assert binding.status_string(binding.LC_ERR_CAPACITY).startswith("basis capacity")
     assert binding.status_string(12345) == "unknown status"

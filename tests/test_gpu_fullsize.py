@@ -114,13 +114,11 @@ def test_random_d64_mixed_matches_fp64_path():
     assert a.dim == b.dim == 4095
     assert oc.ortho_defect(a.basis[:512]) < 1e-12
     np.testing.assert_allclose(a.basis, b.basis, atol=1e-10)
-    # the measured threshold sits above the screen's noise: few dependent
-    # candidates are flagged by noise (each costs an FP64 recheck, never a
-    # wrong decision), and every accepted candidate screened far above tau
+    # the measured threshold sits above the screen's noise (the largest
+    # screened residual among the rejects stays below tau / 2), and every
+    # accepted candidate screened far above tau
     rep = a.report
-    flagged_rejects = rep["n_flagged"] - (a.dim - 2)
-    assert 0 <= flagged_rejects <= 0.01 * a.dim
-    assert rep["max_screen_rej_rel_res"] <= rep["tau_screen"]
+    assert rep["max_screen_rej_rel_res"] < 0.5 * rep["tau_screen"]
     assert rep["min_acc_screen_rel_res"] > 10.0 * rep["tau_screen"]
 
 
