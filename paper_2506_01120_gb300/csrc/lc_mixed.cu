@@ -418,14 +418,20 @@ __global__ void __launch_bounds__(256) k_probe_rows(const double* __restrict__ V
   __shared__ double red[8];
   const int j = blockIdx.x;
   if (threadIdx.x < PROBE_TERMS) {
-    const unsigned long long h = splitmix64(seed ^ splitmix64(((unsigned long long)j << 8) | threadIdx.x));
-    rows[threadIdx.x] = (int)(h % (unsigned long long)N);
+    // single-row probes draw their own row; the combinations share one pool
+    // of rows (drawn with the key 0xFFFF), so for long rows (large d) the pool
+    // is read from L2 instead of once per combination
+    const unsigned long long key = j < S1 ? (unsigned long long)j : 0xFFFFull;
+    const unsigned long long hr = splitmix64(seed ^ splitmix64((key << 8) | threadIdx.x));
+    rows[threadIdx.x] = (int)(hr % (unsigned long long)N);
     // coefficient uniform in [-1, -1/4] U [1/4, 1] (no near-cancellation of the combination)
+    const unsigned long long h = splitmix64(seed ^ splitmix64(((unsigned long long)j << 8) | threadIdx.x));
     const double u = (double)(h >> 11) * (1.0 / 9007199254740992.0);
     coef[threadIdx.x] = (u < 0.5 ? -1.0 : 1.0) * (0.25 + 1.5 * fabs(u - 0.5));
   }
   __syncthreads();
-  const int T = j < S1 ? 1 : PROBE_TERMS;
+  // combinations of PROBE_TERMS pool rows; of 4 for rows longer than 2^16
+  const int T = j < S1 ? 1 : (P > (1 << 16) ? 4 : PROBE_TERMS);
   double ss = 0.0;
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
     double x = 0.0;
