@@ -298,6 +298,7 @@ class Closure {
   unsigned int* bar_ = nullptr;
   double* ws64_ = nullptr;
   static constexpr size_t kWs64 = size_t(2) << 20;   // split-K workspace, doubles
+  static constexpr int kPanel = 128;                  // rows per in-block accept panel
   static constexpr size_t kWsK = size_t(8) << 20;    // split-K partials of the projection, floats (32 MB)
   float* wsk_ = nullptr;
   int* part_ = nullptr;             // per-chunk counts of the multi-CTA compactions
@@ -533,12 +534,44 @@ class Closure {
       LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, rnf_, s_));
     }
     LC_TRY(zero_stats(stats_, n0, s_));
-    LC_TRY(accept_seq(f, R64_, ldp_, rnf_, hnf_, tol_rel2_, tol_abs2_, eta_ * eta_, V64_, ldp_, (int)ncap_, P_,
-                      stats_, st_, bar_, opt.spin_cap, s_, opt.fault_inject ? 1 : 0, alg3_ ? Hraw_ : nullptr,
-                      alg3_ ? B64_ : nullptr, alg3_ ? bn2_ : nullptr, rho2_screen));
-    launches_ += 4;
+    launches_ += 1;
+    // In-block test and append in panels of kPanel rows: the sequential
+    // kernel decides a panel's rows in order (each accept projected out of
+    // the panel's later rows), then the panel's accepted elements W are
+    // projected out of all later rows at once, twice, by FP64 GEMMs.  The
+    // rows' order of decision and their projections are those of the
+    // sequential test; only the grouping of the later rows' projections
+    // changes (one GEMM per panel instead of one rank-1 update per accept).
+    long long nb = n0;
+    int rc = LC_OK;
+    for (int s0 = 0; s0 < f; s0 += kPanel) {
+      const int e0 = std::min(f, s0 + kPanel);
+      const size_t off = (size_t)s0 * ldp_;
+      LC_TRY(accept_seq(e0 - s0, R64_ + off, ldp_, rnf_ + s0, hnf_ + s0, tol_rel2_, tol_abs2_, eta_ * eta_, V64_,
+                        ldp_, (int)ncap_, P_, stats_, st_, bar_, opt.spin_cap, s_,
+                        (s0 == 0 && opt.fault_inject) ? 1 : 0, alg3_ ? Hraw_ + off : nullptr,
+                        alg3_ ? B64_ : nullptr, alg3_ ? bn2_ : nullptr, rho2_screen ? rho2_screen + s0 : nullptr));
+      launches_ += 1;
+      if (e0 >= f) break;
+      rc = sync_read();
+      if (rc != LC_OK) break;
+      const long long na = host_->stats.ncur;
+      const int a = (int)(na - nb);
+      if (a > 0) {
+        const int rest = f - e0;
+        double* Rr = R64_ + (size_t)e0 * ldp_;
+        const double* W = V64_ + (size_t)nb * ldp_;
+        for (int pass = 0; pass < 2; ++pass) {
+          LC_TRY(gemm_nt_f64(rest, a, P_, Rr, ldp_, W, ldp_, beta64_, (int)ncap_, s_, ws64_, kWs64));
+          LC_TRY(gemm_nn_sub_f64(rest, P_, a, beta64_, (int)ncap_, W, ldp_, Rr, ldp_, s_, ws64_, kWs64));
+        }
+        LC_TRY(rownorm2_f64(rest, P_, Rr, ldp_, rnf_ + e0, s_));
+        launches_ += 5;
+      }
+      nb = na;
+    }
     ph_end(PH_ACCEPT);
-    int rc = sync_read();
+    if (rc == LC_OK) rc = sync_read();
     const long long n1 = host_->stats.ncur;
     if (n1 > N_) t_last_accept_ = now_s();
     if (mixed_ && n1 > n0) {

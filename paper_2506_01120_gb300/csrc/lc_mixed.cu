@@ -418,10 +418,12 @@ __global__ void __launch_bounds__(256) k_probe_rows(const double* __restrict__ V
   __shared__ double red[8];
   const int j = blockIdx.x;
   if (threadIdx.x < PROBE_TERMS) {
-    // single-row probes draw their own row; the combinations share one pool
-    // of rows (drawn with the key 0xFFFF), so for long rows (large d) the pool
-    // is read from L2 instead of once per combination
-    const unsigned long long key = j < S1 ? (unsigned long long)j : 0xFFFFull;
+    // every probe draws its own rows, except that for long rows (P > 2^16)
+    // the combinations share one pool (drawn with the key 0xFFFF), read from
+    // L2 instead of from memory once per combination.  (A shared pool at
+    // small P spans too few directions: its eps came out low enough that the
+    // su(128) chain flagged 3.5 times as many candidates by noise.)
+    const unsigned long long key = (j < S1 || P <= (1 << 16)) ? (unsigned long long)j : 0xFFFFull;
     const unsigned long long hr = splitmix64(seed ^ splitmix64((key << 8) | threadIdx.x));
     rows[threadIdx.x] = (int)(hr % (unsigned long long)N);
     // coefficient uniform in [-1, -1/4] U [1/4, 1] (no near-cancellation of the combination)

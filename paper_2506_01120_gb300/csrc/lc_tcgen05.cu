@@ -926,9 +926,9 @@ extern "C" LC_API int lc_split_gemm_f32_noalloc(const float* A, const float* B, 
 // and B with TMA (B through a two-stage ring, so the next unit's operands load
 // during this unit's MMAs); warp 1 issues a unit's 48 MMAs into one of two
 // TMEM accumulators; warps 2-9 drain an accumulator: each thread holds half of
-// one accumulator row (its Re and Im columns) in registers, writes it to a
-// padded shared tile T, and after a barrier reads column j of D from T to
-// write half of packed row j of the bracket:
+// one accumulator row (its Re and Im columns) in registers, writes it
+// transposed into a swizzled shared tile T, and after a barrier reads column j
+// of D from T as 16-byte rows to write half of packed row j of the bracket:
 //   S[j][k] = s2 (Im D[j][k] + Im D[k][j])   (k > j)
 //   S[j][j] = s1 2 Im D[j][j]
 //   S[j][k] = s2 (Re D[j][k] - Re D[k][j])   (k < j)
@@ -945,8 +945,10 @@ constexpr int QP_Y = 4 * QP_BOX;          // Ar hi, Ar lo, Ai hi, Ai lo
 constexpr int QP_XT = 2 * QP_BOX;         // one 128-row X tile (two pairs' 64-row boxes)
 constexpr int QP_X = 4 * QP_XT;           // one X stage: Br hi, Br lo, Bi hi, Bi lo
 constexpr int QP_XSTAGES = 2;
-constexpr int QP_TLD = 129;               // padded row stride of T (floats): conflict-free rows and columns
-constexpr int QP_T = 128 * QP_TLD * 4;    // both pairs' D
+// T holds both pairs' D transposed: row 64 p + c is column c of D_p (Re D_p[k][c]
+// at column k, Im at 64 + k), 4-float groups XOR-swizzled by (row % 8) so that
+// column-wise scalar writes and row-wise 16-byte reads are both conflict-free
+constexpr int QP_T = 128 * 128 * 4;
 constexpr int QP_SMEM = QP_Y + QP_XSTAGES * QP_X + QP_T + 1024;
 constexpr int QP_TMEM = 256;              // two 128-column accumulators
 constexpr int QP_EPI_WARPS = 8;
@@ -1158,28 +1160,43 @@ __global__ void __launch_bounds__(QP_THREADS, 1)
       float re[32], im[32];
       tmem_ld_32cols(taddr, re);
       tmem_ld_32cols(taddr + 64u, im);
-      float* Tr = T + r * QP_TLD + 32 * h;
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
-        Tr[i] = re[i];
-        Tr[Q_D + i] = im[i];
+        const int row = p * 64 + 32 * h + i;                 // column 32h + i of D_p
+        const int sw = (row & 7) << 2;
+        T[row * 128 + (j ^ sw)] = re[i];
+        T[row * 128 + ((Q_D + j) ^ sw)] = im[i];
       }
       tc_fence_before();
       named_bar_sync(1, nthr);                   // T complete; accumulator b free
       if (threadIdx.x == 64) mbar_arrive(&t_empty[b]);
       if (p < n) {
         const long long pidx = w.t + p - t0;     // position of the pair in the block
-        const float* Tc = T + (p * 64 + 32 * h) * QP_TLD + j;   // column j of this pair's D, rows 32h ..
-        __align__(16) __nv_bfloat16 hi[32], lo[32];
+        const int row = p * 64 + j;              // column j of D_p
+        const int sw = (row & 7) << 2;
+        const float* Tj = T + row * 128;
+        __align__(16) __nv_bfloat162 hi[16], lo[16];
         float ss = 0.f;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int k = 32 * h + i;
-          const float re_kj = Tc[i * QP_TLD], im_kj = Tc[i * QP_TLD + Q_D];
-          const float v = (k > j) ? s2 * (im[i] + im_kj) : ((k == j) ? s1 * (im[i] + im_kj) : s2 * (re[i] - re_kj));
-          ss = fmaf(v, v, ss);
-          hi[i] = __float2bfloat16_rn(v);
-          lo[i] = __float2bfloat16_rn(v - __bfloat162float(hi[i]));
+        for (int g = 0; g < 8; ++g) {
+          const int k0 = 32 * h + 4 * g;
+          const float4 rc = *reinterpret_cast<const float4*>(Tj + (k0 ^ sw));          // Re D[k0 ..][j]
+          const float4 ic = *reinterpret_cast<const float4*>(Tj + ((Q_D + k0) ^ sw));  // Im D[k0 ..][j]
+          const float rk[4] = {rc.x, rc.y, rc.z, rc.w}, ik[4] = {ic.x, ic.y, ic.z, ic.w};
+          float v[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int i = 4 * g + e, k = k0 + e;
+            v[e] = (k > j) ? s2 * (im[i] + ik[e]) : ((k == j) ? s1 * (im[i] + ik[e]) : s2 * (re[i] - rk[e]));
+            ss = fmaf(v[e], v[e], ss);
+          }
+#pragma unroll
+          for (int e = 0; e < 4; e += 2) {
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[e], v[e + 1]);
+            const float2 hf = __bfloat1622float2(h2);
+            hi[2 * g + e / 2] = h2;
+            lo[2 * g + e / 2] = __floats2bfloat162_rn(v[e] - hf.x, v[e + 1] - hf.y);
+          }
         }
         __nv_bfloat16* oh = Hhi + pidx * ldh + (long long)j * Q_D + 32 * h;
         __nv_bfloat16* ol = Hlo + pidx * ldh + (long long)j * Q_D + 32 * h;
