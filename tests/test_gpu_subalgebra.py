@@ -83,3 +83,17 @@ def test_subalgebra_d64_closed_form_and_span(kind):
     pre = binding.lie_closure(g, 1e-8, precision="mixed", max_candidates=600, max_dim=1024)
     assert pre.dim == ref.dim
     np.testing.assert_allclose(pre.basis, ref.basis, atol=1e-11, rtol=0)
+
+
+@pytest.mark.parametrize("kind,d,ncand", [("so", 128, 200), ("block", 128, 200), ("so", 256, 60)])
+def test_subalgebra_prefix_large_d(kind, d, ncand):
+    """Subalgebra sets at d = 128 (k_bracket_tc<128>) and d = 256
+    (k_bracket_big): a candidate prefix element by element with the oracle
+    (their full closures, 8128 and more elements, are beyond the oracle)."""
+    g = inputs.random_subalgebra_set(kind, d, 2, seed=d + 1)
+    ref = oc.alg4_orthonormalization(g, 1e-8, max_candidates=ncand)
+    res = binding.lie_closure(g, 1e-8, precision="mixed", max_candidates=ncand, max_dim=512)
+    assert res.dim == ref.dim
+    np.testing.assert_allclose(res.basis, ref.basis, atol=1e-11, rtol=0)
+    if kind == "so":                      # every element real antisymmetric (inside so(d))
+        assert np.max(np.abs(res.basis.imag)) < 1e-12
