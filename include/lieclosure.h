@@ -129,6 +129,12 @@ typedef struct {
                                  band of true residuals the screen could reject
                                  and flags more noise for the FP64 recheck
                                  (time, not correctness) */
+  int accept_kernel;          /* in-block test and append: 0 = by shape
+                                 (default), 1 = one CTA per flagged row,
+                                 2 = every row sliced across all SMs (panels of
+                                 at most 128 rows).  Both take the same
+                                 decisions in the same order and differ only in
+                                 the order of the FP64 partial sums */
 } lc_options;
 
 typedef struct {
@@ -177,6 +183,8 @@ typedef struct {
   int autotuned;              /* 1 if block_k_used and the tile came from the
                                  autotuner (trials in this call or its cache) */
   int autotune_trials;        /* trial blocks this call spent */
+  long long accept_wide_launches; /* in-block accept panels run by the
+                                 row-sliced kernel (accept_kernel) */
 } lc_report;
 
 /* Fills *opt with the defaults listed above. */

@@ -57,7 +57,8 @@ class Options(ctypes.Structure):
                 ("block_k", ctypes.c_int), ("block_k_growth", ctypes.c_int), ("saturation_exit", ctypes.c_int), ("spin_cap", ctypes.c_longlong),
                 ("max_candidates", ctypes.c_longlong), ("verbose", ctypes.c_int), ("profile", ctypes.c_int),
                 ("fault_inject", ctypes.c_int), ("tol_mode", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("ortho_check", ctypes.c_int), ("screen_kappa", ctypes.c_double)]
+                ("ortho_check", ctypes.c_int), ("screen_kappa", ctypes.c_double),
+                ("accept_kernel", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -75,7 +76,8 @@ class Report(ctypes.Structure):
                 ("min_acc_screen_rel_res", ctypes.c_double), ("ortho_defect", ctypes.c_double),
                 ("ortho_rows", ctypes.c_longlong), ("block_k_used", ctypes.c_int),
                 ("block_k_growth_used", ctypes.c_int), ("gemm_tile_n", ctypes.c_int), ("gemm_tile_k", ctypes.c_int),
-                ("autotuned", ctypes.c_int), ("autotune_trials", ctypes.c_int)]
+                ("autotuned", ctypes.c_int), ("autotune_trials", ctypes.c_int),
+                ("accept_wide_launches", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         out = {}

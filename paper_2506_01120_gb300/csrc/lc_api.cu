@@ -232,6 +232,7 @@ class Closure {
       rep->gemm_tile_k = split_gemm_tile_k(gemm_cfg_);
       rep->autotuned = autotuned_ ? 1 : 0;
       rep->autotune_trials = trials_done_;
+      rep->accept_wide_launches = wide_launches_;
       rep->kernel_launches = launches_ + 1 + (N_ > 0 && d_basis_out ? 1 : 0);
       rep->gemm_launches = gemm_launches_;
       rep->gemm_flops = gemm_flops_;
@@ -296,9 +297,11 @@ class Closure {
   double *hn2_ = nullptr, *rn2_ = nullptr, *hnf_ = nullptr, *rnf_ = nullptr, *chk_ = nullptr, *hn2c64_ = nullptr;
   int *idx_ = nullptr, *nonfinite_ = nullptr, *need_ = nullptr;
   unsigned int* bar_ = nullptr;
+  double* wpart_ = nullptr;         // per-CTA partial sums of the row-sliced accept
+  long long wide_launches_ = 0;
   double* ws64_ = nullptr;
   static constexpr size_t kWs64 = size_t(2) << 20;   // split-K workspace, doubles
-  static constexpr int kPanel = 128;                  // rows per in-block accept panel
+  static constexpr int kPanel = kAcceptWideMaxRows;   // rows per in-block accept panel
   static constexpr size_t kWsK = size_t(8) << 20;    // split-K partials of the projection, floats (32 MB)
   float* wsk_ = nullptr;
   int* part_ = nullptr;             // per-chunk counts of the multi-CTA compactions
@@ -329,6 +332,7 @@ class Closure {
     nonfinite_ = ar_.take<int>(1);
     need_ = ar_.take<int>(1);
     bar_ = ar_.take<unsigned int>(2);
+    wpart_ = ar_.take<double>(accept_wide_part_doubles());
     ws64_ = ar_.take<double>(kWs64);
     part_ = ar_.take<int>(3 * kCmpCtas);
     if (alg3_) {
@@ -547,11 +551,14 @@ class Closure {
     for (int s0 = 0; s0 < f; s0 += kPanel) {
       const int e0 = std::min(f, s0 + kPanel);
       const size_t off = (size_t)s0 * ldp_;
+      const int kern = accept_kernel_for(e0 - s0, P_, opt.accept_kernel);
       LC_TRY(accept_seq(e0 - s0, R64_ + off, ldp_, rnf_ + s0, hnf_ + s0, tol_rel2_, tol_abs2_, eta_ * eta_, V64_,
                         ldp_, (int)ncap_, P_, stats_, st_, bar_, opt.spin_cap, s_,
                         (s0 == 0 && opt.fault_inject) ? 1 : 0, alg3_ ? Hraw_ + off : nullptr,
-                        alg3_ ? B64_ : nullptr, alg3_ ? bn2_ : nullptr, rho2_screen ? rho2_screen + s0 : nullptr));
+                        alg3_ ? B64_ : nullptr, alg3_ ? bn2_ : nullptr, rho2_screen ? rho2_screen + s0 : nullptr,
+                        kern, wpart_));
       launches_ += 1;
+      if (kern == 2) wide_launches_ += 1;
       if (e0 >= f) break;
       rc = sync_read();
       if (rc != LC_OK) break;
@@ -937,6 +944,7 @@ int check_args(const void* g, int k, int d, double tol, long long max_dim, const
       o.screen_kappa < 0 || !(o.screen_kappa == o.screen_kappa))
     return LC_ERR_ARG;
   if (o.tol_mode != LC_TOL_RELATIVE && o.tol_mode != LC_TOL_ABSOLUTE) return LC_ERR_ARG;
+  if (o.accept_kernel < 0 || o.accept_kernel > 2) return LC_ERR_ARG;
   if ((long long)d * d > (1ll << 31) / 2) return LC_ERR_ARG;
   return LC_OK;
 }

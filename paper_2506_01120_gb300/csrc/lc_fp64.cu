@@ -565,6 +565,190 @@ __global__ void __launch_bounds__(256) k_accept_seq(int f, double* __restrict__ 
   }
 }
 
+// The same in-block test and append, sliced along the P components instead
+// of the rows: every CTA of the cooperative grid owns one contiguous slice
+// [pb, pe) of every row, so each row streams through all SMs even when only a
+// few candidates are flagged (one CTA per row would leave most SMs idle while
+// it walks rows of 2^20 doubles).  A CTA touches only its own slice of R and
+// V; what crosses CTAs is the per-CTA partial sums of the dot products and
+// squared norms, published through `part` and a grid barrier and summed by
+// every CTA in the same fixed order, so every CTA takes the same decisions.
+// Per accept: phase A partial dots <r_j, w'> (w' = r_i before scaling),
+// barrier; phase B the first projection r_j -= c_j r_i fused with the second
+// pass's partial dots; barrier; phase C the second projection fused with the
+// partial squared norms; barrier.  Per component this is the arithmetic of
+// k_accept_seq; only the order of the partial sums differs.  Threads carry
+// kWideGroup rows at a time so that one CTA reduction serves kWideGroup rows.
+constexpr int kWideGroup = 8;   // 256 threads = 8 warps
+
+__device__ inline void wide_group_store(double (&acc)[kWideGroup], int j0, int jn, double* red, int par,
+                                        double* __restrict__ part, unsigned int G) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double* rb = red + par * 64;    // two 8 x 8 buffers, alternated per group
+#pragma unroll
+  for (int q = 0; q < kWideGroup; ++q) {
+    const double v = warp_sum(acc[q]);
+    if (lane == 0) rb[w * kWideGroup + q] = v;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < jn) {
+    double t = 0.0;
+    for (int ww = 0; ww < 8; ++ww) t += rb[ww * kWideGroup + threadIdx.x];
+    __stcg(&part[(size_t)(j0 + threadIdx.x) * G + blockIdx.x], t);
+  }
+}
+
+// out[j] = sum over CTAs of part[j][.], j in [j_lo, f), in CTA order per lane
+// and a fixed butterfly across lanes (identical in every CTA)
+__device__ inline void wide_sum_partials(const double* __restrict__ part, int j_lo, int f, unsigned int G,
+                                         double* out) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int j = j_lo + w; j < f; j += 8) {
+    double t = 0.0;
+    for (unsigned int g = lane; g < G; g += 32) t += __ldcg(&part[(size_t)j * G + g]);
+    t = warp_sum(t);
+    if (lane == 0) out[j] = t;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_accept_wide(int f, double* __restrict__ R, int ldr,
+                                                     double* __restrict__ rn2, const double* __restrict__ hn2,
+                                                     double tol_rel2, double tol_abs2, double eta2,
+                                                     double* __restrict__ V, int ldv, int ncap, int P,
+                                                     DevStats* stats, DevStatus* st, unsigned int* bar,
+                                                     uint64_t limit_ns, int phantom,
+                                                     const double* __restrict__ Hraw, double* __restrict__ Bk,
+                                                     double* __restrict__ bn2, const float* __restrict__ rho2_screen,
+                                                     double* __restrict__ part) {
+  __shared__ double red[2 * 64];
+  __shared__ double coef[kAcceptWideMaxRows];
+  __shared__ double rn2s[kAcceptWideMaxRows];
+  __shared__ int ok_smem;
+  const unsigned int G = gridDim.x;
+  const unsigned int Gb = G + (unsigned)phantom;   // phantom (test hook): an arrival that never comes
+  const int chunk = (((P + (int)G - 1) / (int)G) + 31) & ~31;
+  const int pb = min(P, (int)blockIdx.x * chunk), pe = min(P, pb + chunk);
+  double* part0 = part;
+  double* part1 = part + (size_t)kAcceptWideMaxRows * G;
+  double* part2 = part + (size_t)2 * kAcceptWideMaxRows * G;
+  const int slot0 = stats->ncur;   // CTA 0 writes it back only after every CTA passed a barrier
+  for (int j = threadIdx.x; j < f; j += blockDim.x) rn2s[j] = rn2[j];
+  __syncthreads();
+  int nacc = 0, nbar = 0;
+  for (int i = 0; i < f; ++i) {
+    const double h2 = hn2[i];
+    const double r2 = rn2s[i];
+    const bool nonzero = h2 > eta2;
+    if (!(nonzero && r2 > tol_rel2 * h2 + tol_abs2)) {
+      if (blockIdx.x == 0 && threadIdx.x == 0 && nonzero) atomicMax(&stats->max_rej_bits, dbits(sqrt(r2 / h2)));
+      continue;
+    }
+    const int slot = slot0 + nacc;
+    if (slot >= ncap) {   // the same test in every CTA
+      if (blockIdx.x == 0 && threadIdx.x == 0 && atomicCAS(&st->code, 0, (int)LC_ERR_CAPACITY) == 0) {
+        st->where = SITE_ACCEPT_CAPACITY;
+        st->info = i;
+      }
+      break;
+    }
+    ++nacc;
+    const double inv = 1.0 / sqrt(r2);
+    const double inv2 = inv * inv;
+    const double* ri = R + (long long)i * ldr;
+    double* v = V + (long long)slot * ldv;
+    for (int p = pb + threadIdx.x; p < pe; p += blockDim.x) v[p] = ri[p] * inv;
+    if (Bk) {   // Algorithm 3: the bracket itself joins B
+      const double* hr = Hraw + (long long)i * ldr;
+      double* b = Bk + (long long)slot * ldv;
+      for (int p = pb + threadIdx.x; p < pe; p += blockDim.x) b[p] = hr[p];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      atomicMin(&stats->min_acc_bits, dbits(sqrt(r2 / h2)));
+      if (rho2_screen) atomicMin(&stats->min_acc_screen_bits, dbits(sqrt((double)rho2_screen[i])));
+      if (Bk) bn2[slot] = h2;
+    }
+    if (i + 1 >= f) break;
+    int par = 0;
+    // phase A: partial <r_i, r_j>
+    for (int j0 = i + 1; j0 < f; j0 += kWideGroup, par ^= 1) {
+      const int jn = min(kWideGroup, f - j0);
+      double acc[kWideGroup];
+#pragma unroll
+      for (int q = 0; q < kWideGroup; ++q) acc[q] = 0.0;
+      for (int p = pb + threadIdx.x; p < pe; p += blockDim.x) {
+        const double x = ri[p];
+#pragma unroll
+        for (int q = 0; q < kWideGroup; ++q)
+          if (q < jn) acc[q] = fma(x, R[(long long)(j0 + q) * ldr + p], acc[q]);
+      }
+      wide_group_store(acc, j0, jn, red, par, part0, G);
+    }
+    ++nbar;
+    if (!grid_barrier(bar, bar + 1, Gb, limit_ns, st, &ok_smem)) return;
+    wide_sum_partials(part0, i + 1, f, G, coef);
+    // phase B: first projection, then partial <r_i, r_j> of the second pass
+    for (int j0 = i + 1; j0 < f; j0 += kWideGroup, par ^= 1) {
+      const int jn = min(kWideGroup, f - j0);
+      double acc[kWideGroup], c[kWideGroup];
+#pragma unroll
+      for (int q = 0; q < kWideGroup; ++q) {
+        acc[q] = 0.0;
+        c[q] = q < jn ? coef[j0 + q] * inv2 : 0.0;
+      }
+      for (int p = pb + threadIdx.x; p < pe; p += blockDim.x) {
+        const double x = ri[p];
+#pragma unroll
+        for (int q = 0; q < kWideGroup; ++q)
+          if (q < jn) {
+            double* rq = R + (long long)(j0 + q) * ldr + p;
+            const double y = fma(-c[q], x, *rq);
+            *rq = y;
+            acc[q] = fma(x, y, acc[q]);
+          }
+      }
+      wide_group_store(acc, j0, jn, red, par, part1, G);
+    }
+    ++nbar;
+    if (!grid_barrier(bar, bar + 1, Gb, limit_ns, st, &ok_smem)) return;
+    wide_sum_partials(part1, i + 1, f, G, coef);
+    // phase C: second projection, then partial ||r_j||^2
+    for (int j0 = i + 1; j0 < f; j0 += kWideGroup, par ^= 1) {
+      const int jn = min(kWideGroup, f - j0);
+      double acc[kWideGroup], c[kWideGroup];
+#pragma unroll
+      for (int q = 0; q < kWideGroup; ++q) {
+        acc[q] = 0.0;
+        c[q] = q < jn ? coef[j0 + q] * inv2 : 0.0;
+      }
+      for (int p = pb + threadIdx.x; p < pe; p += blockDim.x) {
+        const double x = ri[p];
+#pragma unroll
+        for (int q = 0; q < kWideGroup; ++q)
+          if (q < jn) {
+            double* rq = R + (long long)(j0 + q) * ldr + p;
+            const double y = fma(-c[q], x, *rq);
+            *rq = y;
+            acc[q] = fma(y, y, acc[q]);
+          }
+      }
+      wide_group_store(acc, j0, jn, red, par, part2, G);
+    }
+    ++nbar;
+    if (!grid_barrier(bar, bar + 1, Gb, limit_ns, st, &ok_smem)) return;
+    wide_sum_partials(part2, i + 1, f, G, rn2s);
+    if (blockIdx.x == 0)
+      for (int j = i + 1 + (int)threadIdx.x; j < f; j += blockDim.x) rn2[j] = rn2s[j];
+  }
+  if (nacc > 0 && nbar == 0) {   // every CTA must have read ncur before it changes
+    if (!grid_barrier(bar, bar + 1, Gb, limit_ns, st, &ok_smem)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    stats->ncur = slot0 + nacc;
+    stats->naccepted += nacc;
+  }
+}
+
 // Second Gram-Schmidt pass needed?  After one FP64 pass the loss of
 // orthogonality of r is about eps ||h|| / ||r||; when ||r|| >= ||h|| / sqrt(2)
 // for every row (or the row is certainly dependent, ||r|| <= tol ||h|| / 2)
@@ -827,29 +1011,60 @@ cudaError_t screen_compact_f32(const float* hn2, const float* rn2, int count, fl
   return cudaGetLastError();
 }
 
+// co-resident CTAs of a cooperative launch of `kern` (256 threads), per device
+static int coresident_ctas(const void* kern, int which) {
+  static std::mutex mu;
+  static int per_dev[2][128] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return 0;
+  std::lock_guard<std::mutex> g(mu);
+  if (!per_dev[which][dev]) {
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, 0);
+    const int sms = device_sm_count();
+    per_dev[which][dev] = std::max(1, sms * std::max(1, per));
+  }
+  return per_dev[which][dev];
+}
+
+// the sliced kernel runs on at most two CTAs per SM: more CTAs only shorten
+// the slices and lengthen the partial sums and barriers
+static int accept_wide_ctas() {
+  const int co = coresident_ctas((const void*)k_accept_wide, 1);
+  return std::max(1, std::min(co, 2 * device_sm_count()));
+}
+
+size_t accept_wide_part_doubles() { return (size_t)3 * kAcceptWideMaxRows * (size_t)(2 * device_sm_count()); }
+
+// One CTA per row streams a row at one SM's bandwidth and leaves SMs idle
+// when f is small; slicing the rows costs three grid barriers and
+// 3 ceil((f - i - 1) / 8) CTA reductions per accept, which pay off once the
+// rows are long.
+int accept_kernel_for(int f, int P, int requested) {
+  if (f > kAcceptWideMaxRows) return 1;
+  if (requested == 1 || requested == 2) return requested;
+  if (P >= (1 << 18)) return 2;
+  if (P >= (1 << 16) && f <= 32) return 2;
+  return 1;
+}
+
 cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2, double tol_rel2, double tol_abs2,
                        double eta2, double* V, int ldv, int ncap, int P, DevStats* stats, DevStatus* st,
                        unsigned int* bar, long long spin_cap, cudaStream_t s, int phantom, const double* Hraw,
-                       double* Bk, double* bn2, const float* rho2_screen) {
+                       double* Bk, double* bn2, const float* rho2_screen, int kernel, double* wpart) {
   if (f <= 0) return cudaSuccess;
-  // co-resident CTAs of the cooperative launch, per device
-  static std::mutex mu;
-  static int per_dev[128] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
-  int nblocks;
-  {
-    std::lock_guard<std::mutex> g(mu);
-    if (!per_dev[dev]) {
-      int per = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_accept_seq, 256, 0);
-      const int sms = device_sm_count();
-      per_dev[dev] = std::max(1, std::min(sms, sms * per));
-    }
-    nblocks = per_dev[dev];
-  }
-  const int G = std::max(1, std::min(nblocks, f));
   uint64_t lim = spin_cap > 0 ? (uint64_t)spin_cap : 4000000000ull;
+  if (kernel == 2) {
+    if (f > kAcceptWideMaxRows || !wpart) return cudaErrorInvalidValue;
+    const int G = accept_wide_ctas();
+    void* args[] = {&f,    &R,   &ldr,  &rn2,  (void*)&hn2, &tol_rel2, &tol_abs2,          &eta2,
+                    &V,    &ldv, &ncap, &P,    &stats,      &st,       &bar,               &lim,
+                    &phantom, (void*)&Hraw, &Bk, &bn2, (void*)&rho2_screen, &wpart};
+    return cudaLaunchCooperativeKernel((const void*)k_accept_wide, dim3(G), dim3(256), args, 0, s);
+  }
+  const int nblocks = coresident_ctas((const void*)k_accept_seq, 0);
+  if (nblocks <= 0) return cudaErrorInvalidDevice;
+  const int G = std::max(1, std::min(std::min(nblocks, device_sm_count()), f));
   void* args[] = {&f,     &R,   &ldr, &rn2, (void*)&hn2, &tol_rel2,    &tol_abs2, &eta2, &V,   &ldv,
                   &ncap,  &P,   &stats, &st, &bar,       &lim,         &phantom,  (void*)&Hraw, &Bk, &bn2,
                   (void*)&rho2_screen};

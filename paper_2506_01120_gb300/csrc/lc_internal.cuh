@@ -156,12 +156,18 @@ cudaError_t rownorm2_f64(int M, int N, const double* A, int lda, double* out, cu
 // the in-block sequential test-and-append of f flagged rows, one cooperative
 // launch (bar: two zeroed unsigned ints).  Accept iff hn2 > eta2 and
 // rn2 > tol_rel2 * hn2 + tol_abs2 (relative or absolute tolerance);
-// rho2_screen (optional): the rows' screened relative residuals squared
+// rho2_screen (optional): the rows' screened relative residuals squared.
+// kernel: 1 = one CTA per row (k_accept_seq), 2 = every row sliced across the
+// grid (k_accept_wide; f <= kAcceptWideMaxRows, wpart holds
+// accept_wide_part_doubles() doubles), 0 = by shape
+constexpr int kAcceptWideMaxRows = 128;
+size_t accept_wide_part_doubles();
+int accept_kernel_for(int f, int P, int requested);
 cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2, double tol_rel2, double tol_abs2,
                        double eta2, double* V, int ldv, int ncap, int P, DevStats* stats, DevStatus* st,
                        unsigned int* bar, long long spin_cap, cudaStream_t s, int phantom = 0,
                        const double* Hraw = nullptr, double* Bk = nullptr, double* bn2 = nullptr,
-                       const float* rho2_screen = nullptr);
+                       const float* rho2_screen = nullptr, int kernel = 1, double* wpart = nullptr);
 // *need = 1 iff some row needs a second Gram-Schmidt pass
 cudaError_t need_pass2(int f, const double* hn2, const double* rn2, double eta2, double tol_rel2, double tol_abs2,
                        int* need, cudaStream_t s);
