@@ -135,6 +135,14 @@ typedef struct {
                                  at most 128 rows).  Both take the same
                                  decisions in the same order and differ only in
                                  the order of the FP64 partial sums */
+  int fp64_first_pass;        /* mixed mode: nonzero = the first projection of
+                                 flagged candidates is always an FP64 GEMM.
+                                 Default 0: when some flagged row of a block
+                                 needs the second pass anyway (screened
+                                 rho^2 < 1/2) and every one has rho^2 >= 1e-6,
+                                 the first projection takes the screening
+                                 GEMM's coefficients and the FP64 pass follows
+                                 (three FP64 GEMMs instead of four) */
 } lc_options;
 
 typedef struct {
@@ -185,6 +193,8 @@ typedef struct {
   int autotune_trials;        /* trial blocks this call spent */
   long long accept_wide_launches; /* in-block accept panels run by the
                                  row-sliced kernel (accept_kernel) */
+  long long screen_pass1_blocks; /* blocks whose first projection took the
+                                 screening coefficients (fp64_first_pass) */
 } lc_report;
 
 /* Fills *opt with the defaults listed above. */

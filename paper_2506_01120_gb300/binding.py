@@ -58,7 +58,7 @@ class Options(ctypes.Structure):
                 ("max_candidates", ctypes.c_longlong), ("verbose", ctypes.c_int), ("profile", ctypes.c_int),
                 ("fault_inject", ctypes.c_int), ("tol_mode", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("ortho_check", ctypes.c_int), ("screen_kappa", ctypes.c_double),
-                ("accept_kernel", ctypes.c_int)]
+                ("accept_kernel", ctypes.c_int), ("fp64_first_pass", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -77,7 +77,7 @@ class Report(ctypes.Structure):
                 ("ortho_rows", ctypes.c_longlong), ("block_k_used", ctypes.c_int),
                 ("block_k_growth_used", ctypes.c_int), ("gemm_tile_n", ctypes.c_int), ("gemm_tile_k", ctypes.c_int),
                 ("autotuned", ctypes.c_int), ("autotune_trials", ctypes.c_int),
-                ("accept_wide_launches", ctypes.c_longlong)]
+                ("accept_wide_launches", ctypes.c_longlong), ("screen_pass1_blocks", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         out = {}

@@ -233,6 +233,7 @@ class Closure {
       rep->autotuned = autotuned_ ? 1 : 0;
       rep->autotune_trials = trials_done_;
       rep->accept_wide_launches = wide_launches_;
+      rep->screen_pass1_blocks = scr_pass1_blocks_;
       rep->kernel_launches = launches_ + 1 + (N_ > 0 && d_basis_out ? 1 : 0);
       rep->gemm_launches = gemm_launches_;
       rep->gemm_flops = gemm_flops_;
@@ -270,6 +271,8 @@ class Closure {
   double kappa_ = kKappa, tau_max_used_ = 0.0;
   long long N_probe_ = 0, probes_ = 0, gray_ = 0;
   float* rho2f_ = nullptr;            // screened rho^2 of the flagged candidates, flag order
+  int* cidx_ = nullptr;               // compacted (GEMM-row) positions of the flagged candidates
+  long long scr_pass1_blocks_ = 0;    // blocks whose first projection took the screening coefficients
   // orthonormality check
   double* G64_ = nullptr;
   unsigned long long* defect_bits_ = nullptr;
@@ -302,6 +305,8 @@ class Closure {
   double* ws64_ = nullptr;
   static constexpr size_t kWs64 = size_t(2) << 20;   // split-K workspace, doubles
   static constexpr int kPanel = kAcceptWideMaxRows;   // rows per in-block accept panel
+  static constexpr float kScrPass1MaxRho2 = 0.5f;     // a second pass is needed below this
+  static constexpr float kScrPass1MinRho2 = 1e-6f;    // screening coefficients too coarse below this
   static constexpr size_t kWsK = size_t(8) << 20;    // split-K partials of the projection, floats (32 MB)
   float* wsk_ = nullptr;
   int* part_ = nullptr;             // per-chunk counts of the multi-CTA compactions
@@ -363,6 +368,7 @@ class Closure {
       Clo_ = ar_.take<__nv_bfloat16>((size_t)Kpad_ * ldp_);
       hn2c_ = ar_.take<float>(Kpad_);
       rho2f_ = ar_.take<float>(Kpad_);
+      cidx_ = ar_.take<int>(Kpad_);
       wsk_ = ar_.take<float>(kWsK);
       nz_idx_ = ar_.take<int>(Kpad_);
       nnz_ = ar_.take<int>(1);
@@ -517,7 +523,7 @@ class Closure {
   // classical Gram-Schmidt against the basis as it was when the block
   // started (a second pass only when some row needs it), then the in-order
   // test and append against that basis plus this block's accepts.
-  int accept_rows(int f, const float* rho2_screen = nullptr) {
+  int accept_rows(int f, const float* rho2_screen = nullptr, bool scr_coef = false) {
     flagged_ += f;
     ph_begin();
     if (alg3_)   // the raw bracket (or generator) is what Algorithm 3 appends to B
@@ -525,7 +531,17 @@ class Closure {
                                cudaMemcpyDeviceToDevice, s_));
     LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, hnf_, s_));
     const int n0 = (int)N_;
-    if (n0 > 0) {
+    if (n0 > 0 && scr_coef) {
+      // pass 1: h - V c with c the screening GEMM's coefficients (error of
+      // order 1e-5 ||h||, in span(V)); pass 2 in FP64 removes what is left
+      LC_TRY(gather_coef(Bhi_, Blo_, ncap_pad_, cidx_, f, n0, beta64_, (int)ncap_, s_));
+      LC_TRY(gemm_nn_sub_f64(f, P_, n0, beta64_, (int)ncap_, V64_, ldp_, R64_, ldp_, s_, ws64_, kWs64));
+      LC_TRY(gemm_nt_f64(f, n0, P_, R64_, ldp_, V64_, ldp_, beta64_, (int)ncap_, s_, ws64_, kWs64));
+      LC_TRY(gemm_nn_sub_f64(f, P_, n0, beta64_, (int)ncap_, V64_, ldp_, R64_, ldp_, s_, ws64_, kWs64));
+      LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, rnf_, s_));
+      launches_ += 5;
+      scr_pass1_blocks_ += 1;
+    } else if (n0 > 0) {
       LC_TRY(gemm_nt_f64(f, n0, P_, R64_, ldp_, V64_, ldp_, beta64_, (int)ncap_, s_, ws64_, kWs64));
       LC_TRY(gemm_nn_sub_f64(f, P_, n0, beta64_, (int)ncap_, V64_, ldp_, R64_, ldp_, s_, ws64_, kWs64));
       LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, rnf_, s_));
@@ -639,7 +655,18 @@ class Closure {
         LC_TRY(gather_rows_f64(H64_, ldp_, idx_, f, P_, R64_, ldp_, s_));
       }
       launches_ += 1;
-      return accept_rows(f, mixed_ ? rho2f_ : nullptr);
+      // First projection from the screening coefficients when some flagged
+      // row needs a second pass anyway (screened rho^2 < 1/2) and none has a
+      // residual small enough (rho^2 < 1e-6) for the coefficients' BF16-level
+      // error to dominate it.
+      bool scr = false;
+      if (mixed_ && !opt.fp64_first_pass && N_ > 0) {
+        float m;
+        const unsigned int b = host_->stats.min_rho2_flag_bits;
+        memcpy(&m, &b, sizeof(m));
+        scr = m < kScrPass1MaxRho2 && m >= kScrPass1MinRho2;
+      }
+      return accept_rows(f, mixed_ ? rho2f_ : nullptr, scr);
     }
     return LC_OK;
   }
@@ -817,7 +844,7 @@ class Closure {
     LC_TRY(screen_gemms(kb));
     ph_begin();
     LC_TRY(screen_compact_f32(hn2c_, rn2f_, kb, es * es, ts * ts, idx_, stats_, s_, nnz_, nz_idx_,
-                              measured_tau_ ? 1 : 0, rho2f_, part_));
+                              measured_tau_ ? 1 : 0, rho2f_, part_, cidx_));
     ph_end(PH_SCREEN);
     launches_ += 6;     // bracket, compaction (2), gather, screen (2); the GEMMs count themselves
     return after_screen(t0);

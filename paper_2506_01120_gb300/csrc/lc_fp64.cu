@@ -103,8 +103,14 @@ __global__ void k_unpack(const double* __restrict__ V, int n, int d, int ldp, do
 // V[l], V[m], unpacked on the fly), then writes the packed slots of the
 // bracket [V_l, V_m] = C^dagger - C, whose Hermitian part is i (C - C^dagger):
 //   Re H_h[j][k] = -(Im C[j][k] + Im C[k][j]),  Im H_h[j][k] = Re C[j][k] - Re C[k][j].
+// The complex products take three real products instead of four (Gauss):
+// with t1 = sum ar br, t2 = sum ai bi, t3 = sum (ar + ai)(br + bi),
+// Re C = t1 - t2 and Im C = t3 - t1 - t2.  The sums ar + ai, br + bi are
+// formed once when a tile is staged, so the FP64 pipe (the bound of this
+// kernel) runs 3 instead of 4 FMAs per complex multiply-add.  Error: of the
+// order of u (|ar| + |ai|)(|br| + |bi|) per term, i.e. u |A| |B| normwise.
 constexpr int BT = 32;   // tile edge
-constexpr int BQ = 16;   // k-chunk
+constexpr int BQ = 8;    // k-chunk
 
 __device__ inline double2 herm_elem(const double* __restrict__ S, int d, int r, int c, double s1, double s2) {
   if (r >= d || c >= d) return make_double2(0.0, 0.0);
@@ -113,17 +119,19 @@ __device__ inline double2 herm_elem(const double* __restrict__ S, int d, int r, 
   return make_double2(S[(long long)c * d + r] * s2, -S[(long long)r * d + c] * s2);
 }
 
-__device__ inline void cmac(double2& acc, double2 a, double2 b) {
-  acc.x = fma(a.x, b.x, acc.x);
-  acc.x = fma(-a.y, b.y, acc.x);
-  acc.y = fma(a.x, b.y, acc.y);
-  acc.y = fma(a.y, b.x, acc.y);
+struct Gauss3 { double t1, t2, t3; };
+
+__device__ inline void gmac(Gauss3& acc, double ar, double ai, double as, double br, double bi, double bs) {
+  acc.t1 = fma(ar, br, acc.t1);
+  acc.t2 = fma(ai, bi, acc.t2);
+  acc.t3 = fma(as, bs, acc.t3);
 }
 
 __global__ void __launch_bounds__(256) k_bracket_f64(const double* __restrict__ V, int d, int ldv, long long t0,
                                                      const int* __restrict__ idx,
                                                      double* __restrict__ out, int ldo) {
-  __shared__ double2 sAI[BT][BQ + 1], sAJ[BT][BQ + 1], sBI[BQ][BT + 1], sBJ[BQ][BT + 1];
+  // planes: 0 real, 1 imaginary, 2 real + imaginary
+  __shared__ double sAI[3][BT][BQ + 1], sAJ[3][BT][BQ + 1], sBI[3][BQ][BT + 1], sBJ[3][BQ][BT + 1];
   const int pair = blockIdx.y;
   const long long t = t0 + (idx ? idx[pair] : pair);
   int l, m;
@@ -138,27 +146,34 @@ __global__ void __launch_bounds__(256) k_bracket_f64(const double* __restrict__ 
   const int tid = threadIdx.x;
   const int jj = tid >> 3;           // 0..31
   const int kk0 = (tid & 7) * 4;     // 0..28
-  double2 c1[4], c2[4];
+  Gauss3 c1[4], c2[4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) { c1[u] = make_double2(0, 0); c2[u] = make_double2(0, 0); }
+  for (int u = 0; u < 4; ++u) { c1[u] = Gauss3{0, 0, 0}; c2[u] = Gauss3{0, 0, 0}; }
   for (int q0 = 0; q0 < d; q0 += BQ) {
-    for (int e = tid; e < BT * BQ; e += 256) {
-      const int r = e / BQ, c = e % BQ;       // A tiles: row r, col c
-      sAI[r][c] = herm_elem(SA, d, I * BT + r, q0 + c, s1, s2);
-      sAJ[r][c] = herm_elem(SA, d, J * BT + r, q0 + c, s1, s2);
-      const int rb = e / BT, cb = e % BT;     // B tiles: row rb (k), col cb
-      sBI[rb][cb] = herm_elem(SB, d, q0 + rb, I * BT + cb, s1, s2);
-      sBJ[rb][cb] = herm_elem(SB, d, q0 + rb, J * BT + cb, s1, s2);
+    {
+      const int e = tid;                     // BT * BQ = 256 slots per tile
+      const int r = e / BQ, c = e % BQ;      // A tiles: row r, col c
+      double2 v = herm_elem(SA, d, I * BT + r, q0 + c, s1, s2);
+      sAI[0][r][c] = v.x; sAI[1][r][c] = v.y; sAI[2][r][c] = v.x + v.y;
+      v = herm_elem(SA, d, J * BT + r, q0 + c, s1, s2);
+      sAJ[0][r][c] = v.x; sAJ[1][r][c] = v.y; sAJ[2][r][c] = v.x + v.y;
+      const int rb = e / BT, cb = e % BT;    // B tiles: row rb (k), col cb
+      v = herm_elem(SB, d, q0 + rb, I * BT + cb, s1, s2);
+      sBI[0][rb][cb] = v.x; sBI[1][rb][cb] = v.y; sBI[2][rb][cb] = v.x + v.y;
+      v = herm_elem(SB, d, q0 + rb, J * BT + cb, s1, s2);
+      sBJ[0][rb][cb] = v.x; sBJ[1][rb][cb] = v.y; sBJ[2][rb][cb] = v.x + v.y;
     }
     __syncthreads();
-#pragma unroll 4
+#pragma unroll
     for (int q = 0; q < BQ; ++q) {
-      const double2 a1 = sAI[jj][q];
-      const double2 b2 = sBI[q][jj];
+      const double a1r = sAI[0][jj][q], a1i = sAI[1][jj][q], a1s = sAI[2][jj][q];
+      const double b2r = sBI[0][q][jj], b2i = sBI[1][q][jj], b2s = sBI[2][q][jj];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        cmac(c1[u], a1, sBJ[q][kk0 + u]);       // C[I*BT+jj][J*BT+kk]
-        cmac(c2[u], sAJ[kk0 + u][q], b2);       // C[J*BT+kk][I*BT+jj]
+        // C[I*BT+jj][J*BT+kk]
+        gmac(c1[u], a1r, a1i, a1s, sBJ[0][q][kk0 + u], sBJ[1][q][kk0 + u], sBJ[2][q][kk0 + u]);
+        // C[J*BT+kk][I*BT+jj]
+        gmac(c2[u], sAJ[0][kk0 + u][q], sAJ[1][kk0 + u][q], sAJ[2][kk0 + u][q], b2r, b2i, b2s);
       }
     }
     __syncthreads();
@@ -169,11 +184,13 @@ __global__ void __launch_bounds__(256) k_bracket_f64(const double* __restrict__ 
   for (int u = 0; u < 4; ++u) {
     const int j = I * BT + jj, k = J * BT + kk0 + u;
     if (j >= d || k >= d) continue;
+    const double c1x = c1[u].t1 - c1[u].t2, c1y = c1[u].t3 - c1[u].t1 - c1[u].t2;
+    const double c2x = c2[u].t1 - c2[u].t2, c2y = c2[u].t3 - c2[u].t1 - c2[u].t2;
     if (j < k) {
-      O[(long long)j * d + k] = -(c1[u].y + c2[u].y) * o2;
-      O[(long long)k * d + j] = (c1[u].x - c2[u].x) * o2;
+      O[(long long)j * d + k] = -(c1y + c2y) * o2;
+      O[(long long)k * d + j] = (c1x - c2x) * o2;
     } else if (j == k) {
-      O[(long long)j * d + j] = -2.0 * c1[u].y * o1;
+      O[(long long)j * d + j] = -2.0 * c1y * o1;
     }
   }
 }
@@ -409,6 +426,7 @@ __global__ void __launch_bounds__(kCmpThreads) k_screen_pass1(const T* __restric
     part[kCmpCtas + blockIdx.x] = b;
     part[2 * kCmpCtas + blockIdx.x] = g;
     if (m > 0.0) atomicMax(&stats->max_screen_rej_bits, dbits(m));
+    if (blockIdx.x == 0) stats->min_rho2_flag_bits = 0x7f800000u;   // +inf, lowered by pass 2
   }
 }
 
@@ -419,9 +437,11 @@ __global__ void __launch_bounds__(kCmpThreads) k_screen_pass2(const T* __restric
                                                            const int* __restrict__ count_dev,
                                                            const int* __restrict__ map, int measured,
                                                            float* __restrict__ rho2_flag,
-                                                           const int* __restrict__ part) {
+                                                           const int* __restrict__ part, int* __restrict__ cidx) {
   __shared__ int wsum[kCmpThreads / 32];
+  __shared__ unsigned int wmin[kCmpThreads / 32];
   __shared__ int base;
+  unsigned int rmin = 0x7f800000u;   // float bits of the smallest flagged rho^2 this thread saw
   if (count_dev) count = min(count, *count_dev);
   if (measured) tau2 = (T)stats->tau2;
   const int chunk = (count + gridDim.x - 1) / gridDim.x;
@@ -446,10 +466,25 @@ __global__ void __launch_bounds__(kCmpThreads) k_screen_pass2(const T* __restric
     const int at = base + cta_excl_scan(f, &tot, wsum);
     if (f) {
       idx[at] = map ? map[c] : c;
-      if (rho2_flag) rho2_flag[at] = (float)((double)rn2[c] / (double)hn2[c]);
+      if (cidx) cidx[at] = c;
+      if (rho2_flag) {
+        const float r = (float)((double)rn2[c] / (double)hn2[c]);
+        rho2_flag[at] = r;
+        rmin = min(rmin, __float_as_uint(r));   // non-negative floats order as their bits
+      }
     }
     if (threadIdx.x == 0) base += tot;
     __syncthreads();
+  }
+  if (rho2_flag) {
+    for (int o = 16; o > 0; o >>= 1) rmin = min(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+    if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = rmin;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned int m = wmin[0];
+      for (int i = 1; i < kCmpThreads / 32; ++i) m = min(m, wmin[i]);
+      if (m != 0x7f800000u) atomicMin(&stats->min_rho2_flag_bits, m);
+    }
   }
 }
 
@@ -988,7 +1023,7 @@ cudaError_t screen_compact_f64(const double* hn2, const double* rn2, int count, 
     k_screen_pass1<double><<<kCmpCtas, kCmpThreads, 0, s>>>(hn2, rn2, count, eta2, tau2, tau2_abs, stats, count_dev,
                                                             0, part);
     k_screen_pass2<double><<<kCmpCtas, kCmpThreads, 0, s>>>(hn2, rn2, count, eta2, tau2, tau2_abs, idx, stats,
-                                                            count_dev, map, 0, nullptr, part);
+                                                            count_dev, map, 0, nullptr, part, nullptr);
     return cudaGetLastError();
   }
   k_screen_compact<double><<<1, 1024, 0, s>>>(hn2, rn2, count, eta2, tau2, tau2_abs, idx, stats, count_dev, map, 0,
@@ -998,14 +1033,15 @@ cudaError_t screen_compact_f64(const double* hn2, const double* rn2, int count, 
 
 cudaError_t screen_compact_f32(const float* hn2, const float* rn2, int count, float eta2, float tau2, int* idx,
                                DevStats* stats, cudaStream_t s, const int* count_dev, const int* map, int measured,
-                               float* rho2_flag, int* part) {
+                               float* rho2_flag, int* part, int* cidx) {
   if (part) {
     k_screen_pass1<float><<<kCmpCtas, kCmpThreads, 0, s>>>(hn2, rn2, count, eta2, tau2, 0.f, stats, count_dev,
                                                            measured, part);
     k_screen_pass2<float><<<kCmpCtas, kCmpThreads, 0, s>>>(hn2, rn2, count, eta2, tau2, 0.f, idx, stats, count_dev,
-                                                           map, measured, rho2_flag, part);
+                                                           map, measured, rho2_flag, part, cidx);
     return cudaGetLastError();
   }
+  if (cidx) return cudaErrorInvalidValue;   // the single-CTA form writes no compacted positions
   k_screen_compact<float><<<1, 1024, 0, s>>>(hn2, rn2, count, eta2, tau2, 0.f, idx, stats, count_dev, map,
                                              measured, rho2_flag);
   return cudaGetLastError();

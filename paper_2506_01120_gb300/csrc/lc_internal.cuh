@@ -56,7 +56,7 @@ struct DevStats {
   int ngray;           // screen rejects in (eps, tau] in the current block
   float tau2;          // measured screen threshold tau^2 (mixed mode)
   float eps2;          // latest probe's eps^2
-  int pad_;
+  unsigned int min_rho2_flag_bits;  // float bits: smallest screened rho^2 among the block's flagged rows
 };
 
 // pair index t = l(l-1)/2 + m, 0 <= m < l  <->  (l, m)
@@ -191,7 +191,7 @@ cudaError_t compact_nonzero_f64(const double* hn2, int count, double eta2, int* 
 cudaError_t screen_compact_f32(const float* hn2, const float* rn2, int count, float eta2,
                                float tau2, int* idx, DevStats* stats, cudaStream_t s,
                                const int* count_dev = nullptr, const int* map = nullptr, int measured = 0,
-                               float* rho2_flag = nullptr, int* part = nullptr);
+                               float* rho2_flag = nullptr, int* part = nullptr, int* cidx = nullptr);
 cudaError_t zero_stats(DevStats* stats, int ncur, cudaStream_t s);
 
 // ------------------------------------------------------ mixed-precision path
@@ -239,6 +239,10 @@ cudaError_t compact_nonzero(const float* hn2, int count, float eta2, int* nz_idx
 cudaError_t gather_candidates(const __nv_bfloat16* Hhi, const __nv_bfloat16* Hlo, int ldh, const float* hn2,
                               const int* nz_idx, const int* nnz, int count, int ncols, __nv_bfloat16* Chi,
                               __nv_bfloat16* Clo, float* hn2c, cudaStream_t s);
+// beta (f x n, FP64, row stride ldb) = the screening coefficients D = H V^T
+// (BF16 hi + lo, row stride ldd) of the compacted rows cidx[0..f)
+cudaError_t gather_coef(const __nv_bfloat16* Dhi, const __nv_bfloat16* Dlo, int ldd, const int* cidx, int f, int n,
+                        double* beta, int ldb, cudaStream_t s);
 // tensor-core brackets (d = 64, 128) from the embeddings E (nelems elements)
 bool bracket_tc_supported(int d);
 cudaError_t bracket_tc(const __nv_bfloat16* Ehi, const __nv_bfloat16* Elo, long long nelems, int d, long long t0,

@@ -389,6 +389,26 @@ cudaError_t gather_candidates(const __nv_bfloat16* Hhi, const __nv_bfloat16* Hlo
   return cudaGetLastError();
 }
 
+// beta[i][j] = hi + lo of the screening GEMM's coefficient <h_c, v_j> of the
+// flagged row i (compacted position c = cidx[i]), j < n, in FP64
+__global__ void k_gather_coef(const __nv_bfloat16* __restrict__ Dhi, const __nv_bfloat16* __restrict__ Dlo, int ldd,
+                              const int* __restrict__ cidx, int f, int n, double* __restrict__ beta, int ldb) {
+  for (int i = blockIdx.y; i < f; i += gridDim.y) {
+    const long long c = cidx[i];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+      beta[(long long)i * ldb + j] =
+          (double)__bfloat162float(Dhi[c * ldd + j]) + (double)__bfloat162float(Dlo[c * ldd + j]);
+  }
+}
+
+cudaError_t gather_coef(const __nv_bfloat16* Dhi, const __nv_bfloat16* Dlo, int ldd, const int* cidx, int f, int n,
+                        double* beta, int ldb, cudaStream_t s) {
+  if (f <= 0 || n <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)std::min((n + 255) / 256, 64), (unsigned)std::min(f, 65535));
+  k_gather_coef<<<grid, 256, 0, s>>>(Dhi, Dlo, ldd, cidx, f, n, beta, ldb);
+  return cudaGetLastError();
+}
+
 }  // namespace lc
 
 // ------------------------------------------------------ screen noise probe

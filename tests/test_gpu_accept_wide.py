@@ -1,5 +1,7 @@
-"""GPU parity of the row-sliced in-block accept kernel (k_accept_wide, option
-accept_kernel = 2) against the oracle, through the C ABI.
+"""GPU parity of the accept path's alternatives against the oracle, through
+the C ABI: the row-sliced in-block accept kernel (k_accept_wide, option
+accept_kernel = 2) and the first projection taken from the screening GEMM's
+coefficients (default in mixed mode, off with fp64_first_pass).
 
 The sliced kernel takes the in-block decisions of Algorithm 4 in the same
 order as the one-CTA-per-row kernel; only the order of the FP64 partial sums
@@ -134,3 +136,32 @@ def test_sliced_accept_dense_d256_prefix():
     assert a.report["accept_wide_launches"] > 0
     assert a.dim == ref.dim > 40
     np.testing.assert_allclose(a.basis, ref.basis, atol=1e-11, rtol=0)
+
+
+# ------------------------------------------------ first projection from the screen
+@pytest.mark.parametrize("name", ["rand_d8", "rand_d16_prefix", "rand_d6_k3"])
+def test_screen_coefficient_first_pass_matches_oracle(name):
+    """Mixed mode, blocks whose flagged rows need a second Gram-Schmidt pass
+    (screened rho^2 < 1/2, i.e. more than half of the space spanned) take
+    the screening GEMM's coefficients as the first projection and one FP64
+    pass after it; the basis is the oracle's element by element and the same
+    as with the FP64 first pass (option fp64_first_pass).  (Pauli-string sets
+    never take it: their flagged rows have rho = 1.)"""
+    g, tol, ncand = _case(name)
+    kw = {} if ncand is None else {"max_candidates": ncand}
+    ref = oc.alg4_orthonormalization(g, tol, **kw)
+    a = binding.lie_closure(g, tol, precision="mixed", ortho_check=1, **kw)
+    assert a.report["screen_pass1_blocks"] > 0
+    assert a.dim == ref.dim
+    np.testing.assert_allclose(a.basis, ref.basis, atol=1e-11, rtol=0)
+    assert a.report["ortho_defect"] < 1e-12
+    b = binding.lie_closure(g, tol, precision="mixed", fp64_first_pass=1, **kw)
+    assert b.report["screen_pass1_blocks"] == 0
+    assert b.dim == a.dim
+    np.testing.assert_allclose(a.basis, b.basis, atol=1e-11, rtol=0)
+
+
+def test_fp64_mode_never_takes_screen_coefficients():
+    g, tol, ncand = _case("rand_d16_prefix")
+    r = binding.lie_closure(g, tol, precision="fp64", max_candidates=ncand)
+    assert r.report["screen_pass1_blocks"] == 0
