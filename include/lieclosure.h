@@ -143,6 +143,12 @@ typedef struct {
                                  the first projection takes the screening
                                  GEMM's coefficients and the FP64 pass follows
                                  (three FP64 GEMMs instead of four) */
+  int accept_gemm;            /* mixed mode, projections of the flagged rows
+                                 against V (c = R V^T, R -= c V): 0 (default) =
+                                 FP64-accurate BF16 tensor-core GEMMs
+                                 (lc_gemm_f64_tc's digit slicing) at d = 64 ..
+                                 128 when the product is large; 1 = FP64 SIMT
+                                 GEMMs always.  FP64 mode always uses FP64 SIMT */
 } lc_options;
 
 typedef struct {
@@ -195,6 +201,8 @@ typedef struct {
                                  row-sliced kernel (accept_kernel) */
   long long screen_pass1_blocks; /* blocks whose first projection took the
                                  screening coefficients (fp64_first_pass) */
+  long long accept_tc_gemms;  /* projections run as FP64-accurate tensor-core
+                                 GEMMs (accept_gemm) */
 } lc_report;
 
 /* Fills *opt with the defaults listed above. */

@@ -31,6 +31,27 @@ extern "C" {
 LC_API int lc_split_gemm_f32(const float* A, const float* B, int M, int N, int K, float* D, void* stream);
 
 /*
+ * lc_gemm_f64_tc -- C = A B^T to FP64 accuracy on the BF16 tensor cores: the
+ * product the FP64 Gram-Schmidt of the accept step (c = R V^T, R -= c V,
+ * Section 3.2) runs on in mixed mode.  Each row is scaled by a power of two
+ * and cut into S balanced base-2^beta digit slices, exact in BF16
+ * (beta = 7, S = 8 for K <= 4096; beta = 6, S = 9 above); every slice pair
+ * with s + t <= S - 1 is one tcgen05.mma chain whose FP32 accumulation is
+ * exact (K 2^{2 beta - 2} <= 2^24 per chain; longer K is split), and the
+ * chains are summed in FP64.  The error is of the order of 2^-53 times the
+ * row-scale bound K max|a_i.| max|b_j.|, like an FP64 dot product's.
+ *
+ * A : M x K FP64, row-major, device pointer (row stride K).
+ * B : N x K FP64, row-major, device pointer (row stride K).
+ * C : M x N FP64, row-major, device pointer (row stride N), written.
+ * Any M, N, K >= 1.  Workspace (slices, partials) is allocated and freed
+ * within the call on `stream` (cudaStream_t as void*, NULL = legacy default);
+ * the call returns after the stream has finished.
+ * Returns LC_OK, LC_ERR_ARG, LC_ERR_OOM, LC_ERR_CUDA or LC_ERR_TIMEOUT.
+ */
+LC_API int lc_gemm_f64_tc(const double* A, const double* B, int M, int N, int K, double* C, void* stream);
+
+/*
  * lc_split_gemm_f32_noalloc -- lc_split_gemm_f32 without any device memory
  * allocation.  The paper has no counterpart; this exists for callers that
  * cannot let a library allocate: a process whose own pool already owns the

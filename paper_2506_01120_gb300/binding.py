@@ -39,7 +39,7 @@ EXPORTED = ["lc_default_options", "lc_status_string", "lc_version", "lie_closure
             "lie_closure_batched", "lie_closure_batched_dev", "lie_closure_alg2", "lie_closure_alg2_dev", "lie_closure_alg3",
             "lie_closure_alg3_dev", "lie_closure_resume",
             "lie_closure_resume_dev", "lie_closure_pauli", "lie_closure_pauli_dev", "lc_split_gemm_f32",
-            "lc_split_gemm_f32_noalloc"]
+            "lc_split_gemm_f32_noalloc", "lc_gemm_f64_tc"]
 
 
 class LibraryNotBuilt(RuntimeError):
@@ -58,7 +58,8 @@ class Options(ctypes.Structure):
                 ("max_candidates", ctypes.c_longlong), ("verbose", ctypes.c_int), ("profile", ctypes.c_int),
                 ("fault_inject", ctypes.c_int), ("tol_mode", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("ortho_check", ctypes.c_int), ("screen_kappa", ctypes.c_double),
-                ("accept_kernel", ctypes.c_int), ("fp64_first_pass", ctypes.c_int)]
+                ("accept_kernel", ctypes.c_int), ("fp64_first_pass", ctypes.c_int),
+                ("accept_gemm", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -77,7 +78,8 @@ class Report(ctypes.Structure):
                 ("ortho_rows", ctypes.c_longlong), ("block_k_used", ctypes.c_int),
                 ("block_k_growth_used", ctypes.c_int), ("gemm_tile_n", ctypes.c_int), ("gemm_tile_k", ctypes.c_int),
                 ("autotuned", ctypes.c_int), ("autotune_trials", ctypes.c_int),
-                ("accept_wide_launches", ctypes.c_longlong), ("screen_pass1_blocks", ctypes.c_longlong)]
+                ("accept_wide_launches", ctypes.c_longlong), ("screen_pass1_blocks", ctypes.c_longlong),
+                ("accept_tc_gemms", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         out = {}
@@ -143,6 +145,8 @@ def lib():
         L.lc_split_gemm_f32.argtypes = [c_p, c_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_p, c_p]
         L.lc_split_gemm_f32.restype = ctypes.c_int
         L.lc_split_gemm_f32_noalloc.argtypes = L.lc_split_gemm_f32.argtypes
+        L.lc_gemm_f64_tc.argtypes = L.lc_split_gemm_f32.argtypes
+        L.lc_gemm_f64_tc.restype = ctypes.c_int
         L.lc_split_gemm_f32_noalloc.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -456,6 +460,25 @@ def lc_split_gemm_f32(A, B, stream=None):
     st = lib().lc_split_gemm_f32(A.data_ptr(), B.data_ptr(), M, N, K, D.data_ptr(), ctypes.c_void_p(s.cuda_stream))
     _check(st, True)
     return D
+
+
+def lc_gemm_f64_tc(A, B, stream=None):
+    """C = A B^T (torch FP64 CUDA tensors) to FP64 accuracy through the sliced
+    BF16 tensor-core GEMM."""
+    import torch
+    if not (A.is_cuda and B.is_cuda and A.dtype == torch.float64 and B.dtype == torch.float64):
+        raise ValueError("A and B must be float64 CUDA tensors")
+    A = A.contiguous()
+    B = B.contiguous()
+    M, K = A.shape
+    N, K2 = B.shape
+    if K != K2:
+        raise ValueError("inner dimensions differ")
+    C = torch.empty((M, N), dtype=torch.float64, device=A.device)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = lib().lc_gemm_f64_tc(A.data_ptr(), B.data_ptr(), M, N, K, C.data_ptr(), ctypes.c_void_p(s.cuda_stream))
+    _check(st, True)
+    return C
 
 
 def lc_split_gemm_f32_noalloc(A, B, stream=None, check: bool = True):

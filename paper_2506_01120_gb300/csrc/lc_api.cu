@@ -157,6 +157,14 @@ class Closure {
     big_bracket_ = mixed_ && !bracket_tc_supported(d) && bracket_big_supported(d);
     tc_bracket_ = mixed_ && (bracket_tc_supported(d) || big_bracket_);
     q_bracket_ = mixed_ && d == 64;      // [Hr; Hi] operands instead of the 2d x 2d embedding
+    // FP64-accurate tensor-core GEMMs for the accept step's projections in
+    // mixed mode at d = 64 .. 128 (the V slices take 4 S P ncap bytes)
+    if (mixed_ && o.accept_gemm == 0 && P_ >= 4096 && P_ <= 16384) {
+      oz_beta_ = oz_beta_for((int)std::max<long long>(P_, ncap_));
+      oz_S_ = oz_slices_for(oz_beta_);
+      const double vbytes = 4.0 * oz_S_ * (double)ldp_ * (double)ncap_pad_;
+      oz_on_ = vbytes <= 12.0e9;
+    }
   }
 
   // Resume: d_gens holds n_resume orthonormal basis elements returned by an
@@ -234,6 +242,7 @@ class Closure {
       rep->autotune_trials = trials_done_;
       rep->accept_wide_launches = wide_launches_;
       rep->screen_pass1_blocks = scr_pass1_blocks_;
+      rep->accept_tc_gemms = oz_gemms_;
       rep->kernel_launches = launches_ + 1 + (N_ > 0 && d_basis_out ? 1 : 0);
       rep->gemm_launches = gemm_launches_;
       rep->gemm_flops = gemm_flops_;
@@ -272,6 +281,17 @@ class Closure {
   long long N_probe_ = 0, probes_ = 0, gray_ = 0;
   float* rho2f_ = nullptr;            // screened rho^2 of the flagged candidates, flag order
   int* cidx_ = nullptr;               // compacted (GEMM-row) positions of the flagged candidates
+  // FP64-accurate tensor-core GEMMs of the accept step (digit slices): V's
+  // rows and transposed rows with a fixed exponent (|v| <= 1), flagged rows
+  // and their coefficients in chunks of kOzRows with per-row exponents
+  static constexpr int kOzRows = 2048;
+  static constexpr size_t kOzWs = size_t(8) << 20;   // split-K partials, doubles (64 MB)
+  bool oz_on_ = false;
+  int oz_beta_ = 0, oz_S_ = 0, oz_rows_ = 0;
+  __nv_bfloat16 *Vs_ = nullptr, *VsT_ = nullptr, *Rs_ = nullptr, *Cs_ = nullptr;
+  int *eR_ = nullptr, *eC_ = nullptr;
+  double* oz_ws_ = nullptr;
+  long long oz_gemms_ = 0;
   long long scr_pass1_blocks_ = 0;    // blocks whose first projection took the screening coefficients
   // orthonormality check
   double* G64_ = nullptr;
@@ -369,6 +389,15 @@ class Closure {
       hn2c_ = ar_.take<float>(Kpad_);
       rho2f_ = ar_.take<float>(Kpad_);
       cidx_ = ar_.take<int>(Kpad_);
+      if (oz_on_) {
+        Vs_ = ar_.take<__nv_bfloat16>((size_t)oz_S_ * ncap_pad_ * ldp_);
+        VsT_ = ar_.take<__nv_bfloat16>((size_t)oz_S_ * ldp_ * ncap_pad_);
+        Rs_ = ar_.take<__nv_bfloat16>((size_t)oz_S_ * kOzRows * ldp_);
+        Cs_ = ar_.take<__nv_bfloat16>((size_t)oz_S_ * kOzRows * ncap_pad_);
+        eR_ = ar_.take<int>(kOzRows);
+        eC_ = ar_.take<int>(kOzRows);
+        oz_ws_ = ar_.take<double>(kOzWs);
+      }
       wsk_ = ar_.take<float>(kWsK);
       nz_idx_ = ar_.take<int>(Kpad_);
       nnz_ = ar_.take<int>(1);
@@ -519,6 +548,62 @@ class Closure {
     ev_pool_.clear();
   }
 
+  // V rows [oz_rows_, n0) into both slice layouts (rows are final once appended)
+  cudaError_t oz_sync_v(int n0) {
+    if (n0 <= oz_rows_) return cudaSuccess;
+    cudaError_t e = oz_slice_rows(V64_ + (size_t)oz_rows_ * ldp_, n0 - oz_rows_, P_, ldp_, oz_S_, oz_beta_, 1, Vs_,
+                                  ncap_pad_, ldp_, nullptr, oz_rows_, nullptr, s_);
+    if (e == cudaSuccess)
+      e = oz_slice_cols(V64_, oz_rows_, n0, P_, ldp_, oz_S_, oz_beta_, 1, VsT_, ldp_, ncap_pad_, s_);
+    launches_ += 2;
+    oz_rows_ = n0;
+    return e;
+  }
+  // the tensor-core form where the FP64 product is long enough to pay for
+  // the slicing (about 2^30 multiply-adds and up)
+  bool oz_use(int f, int n0) const { return oz_on_ && n0 >= 64 && (double)f * n0 * P_ >= 1073741824.0; }
+
+  // beta64 rows [0, f) = R64 rows [0, f) V[0, n0)^T
+  cudaError_t proj_coef(int f, int n0, const int* run_if = nullptr) {
+    if (!oz_use(f, n0)) {
+      launches_ += 1;
+      return gemm_nt_f64(f, n0, P_, R64_, ldp_, V64_, ldp_, beta64_, (int)ncap_, s_, ws64_, kWs64, run_if);
+    }
+    cudaError_t e = oz_sync_v(n0);
+    for (int r0 = 0; r0 < f && e == cudaSuccess; r0 += kOzRows) {
+      const int c = std::min(kOzRows, f - r0);
+      e = oz_slice_rows(R64_ + (size_t)r0 * ldp_, c, P_, ldp_, oz_S_, oz_beta_, 0, Rs_, kOzRows, ldp_, eR_, 0,
+                        run_if, s_);
+      launches_ += 1;
+      if (e != cudaSuccess) break;
+      const OzOperand A{Rs_, kOzRows, ldp_, eR_, 0}, B{Vs_, ncap_pad_, ldp_, nullptr, 1};
+      e = ozaki_gemm_nt(c, n0, P_, A, B, oz_S_, oz_beta_, beta64_ + (size_t)r0 * ncap_, (int)ncap_, false, oz_ws_,
+                        kOzWs, run_if, opt.spin_cap, st_, s_, &launches_);
+      oz_gemms_ += 1;
+    }
+    return e;
+  }
+  // R64 rows [0, f) -= beta64 rows [0, f) V[0, n0)
+  cudaError_t proj_sub(int f, int n0, const int* run_if = nullptr) {
+    if (!oz_use(f, n0)) {
+      launches_ += 1;
+      return gemm_nn_sub_f64(f, P_, n0, beta64_, (int)ncap_, V64_, ldp_, R64_, ldp_, s_, ws64_, kWs64, run_if);
+    }
+    cudaError_t e = oz_sync_v(n0);
+    for (int r0 = 0; r0 < f && e == cudaSuccess; r0 += kOzRows) {
+      const int c = std::min(kOzRows, f - r0);
+      e = oz_slice_rows(beta64_ + (size_t)r0 * ncap_, c, n0, (int)ncap_, oz_S_, oz_beta_, 0, Cs_, kOzRows,
+                        ncap_pad_, eC_, 0, run_if, s_);
+      launches_ += 1;
+      if (e != cudaSuccess) break;
+      const OzOperand A{Cs_, kOzRows, ncap_pad_, eC_, 0}, B{VsT_, ldp_, ncap_pad_, nullptr, 1};
+      e = ozaki_gemm_nt(c, P_, n0, A, B, oz_S_, oz_beta_, R64_ + (size_t)r0 * ldp_, ldp_, true, oz_ws_, kOzWs,
+                        run_if, opt.spin_cap, st_, s_, &launches_);
+      oz_gemms_ += 1;
+    }
+    return e;
+  }
+
   // Test-and-append of the f candidate rows in R64 (FP64, pair order):
   // classical Gram-Schmidt against the basis as it was when the block
   // started (a second pass only when some row needs it), then the in-order
@@ -535,21 +620,21 @@ class Closure {
       // pass 1: h - V c with c the screening GEMM's coefficients (error of
       // order 1e-5 ||h||, in span(V)); pass 2 in FP64 removes what is left
       LC_TRY(gather_coef(Bhi_, Blo_, ncap_pad_, cidx_, f, n0, beta64_, (int)ncap_, s_));
-      LC_TRY(gemm_nn_sub_f64(f, P_, n0, beta64_, (int)ncap_, V64_, ldp_, R64_, ldp_, s_, ws64_, kWs64));
-      LC_TRY(gemm_nt_f64(f, n0, P_, R64_, ldp_, V64_, ldp_, beta64_, (int)ncap_, s_, ws64_, kWs64));
-      LC_TRY(gemm_nn_sub_f64(f, P_, n0, beta64_, (int)ncap_, V64_, ldp_, R64_, ldp_, s_, ws64_, kWs64));
+      LC_TRY(proj_sub(f, n0));
+      LC_TRY(proj_coef(f, n0));
+      LC_TRY(proj_sub(f, n0));
       LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, rnf_, s_));
-      launches_ += 5;
+      launches_ += 2;
       scr_pass1_blocks_ += 1;
     } else if (n0 > 0) {
-      LC_TRY(gemm_nt_f64(f, n0, P_, R64_, ldp_, V64_, ldp_, beta64_, (int)ncap_, s_, ws64_, kWs64));
-      LC_TRY(gemm_nn_sub_f64(f, P_, n0, beta64_, (int)ncap_, V64_, ldp_, R64_, ldp_, s_, ws64_, kWs64));
+      LC_TRY(proj_coef(f, n0));
+      LC_TRY(proj_sub(f, n0));
       LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, rnf_, s_));
       LC_TRY(need_pass2(f, hnf_, rnf_, eta_ * eta_, tol_rel2_, tol_abs2_, need_, s_));
-      LC_TRY(gemm_nt_f64(f, n0, P_, R64_, ldp_, V64_, ldp_, beta64_, (int)ncap_, s_, ws64_, kWs64, need_));
-      LC_TRY(gemm_nn_sub_f64(f, P_, n0, beta64_, (int)ncap_, V64_, ldp_, R64_, ldp_, s_, ws64_, kWs64, need_));
+      LC_TRY(proj_coef(f, n0, need_));
+      LC_TRY(proj_sub(f, n0, need_));
       LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, rnf_, s_, need_));
-      launches_ += 10;
+      launches_ += 4;
     } else {
       LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, rnf_, s_));
     }
@@ -972,6 +1057,7 @@ int check_args(const void* g, int k, int d, double tol, long long max_dim, const
     return LC_ERR_ARG;
   if (o.tol_mode != LC_TOL_RELATIVE && o.tol_mode != LC_TOL_ABSOLUTE) return LC_ERR_ARG;
   if (o.accept_kernel < 0 || o.accept_kernel > 2) return LC_ERR_ARG;
+  if (o.accept_gemm < 0 || o.accept_gemm > 1) return LC_ERR_ARG;
   if ((long long)d * d > (1ll << 31) / 2) return LC_ERR_ARG;
   return LC_OK;
 }

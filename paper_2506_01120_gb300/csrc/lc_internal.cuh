@@ -194,6 +194,35 @@ cudaError_t screen_compact_f32(const float* hn2, const float* rn2, int count, fl
                                float* rho2_flag = nullptr, int* part = nullptr, int* cidx = nullptr);
 cudaError_t zero_stats(DevStats* stats, int ncur, cudaStream_t s);
 
+// ------------------------------------------------------ FP64-accurate tensor-core GEMM
+// (lc_tcgen05.cu)  An operand as a stack of S BF16 digit slices: slice s of
+// row i at slices[(s * rows + i) * ld + k]; row i's value is
+// 2^{e_i} sum_s 2^{-beta (s+1)} d_s(i, k) with e_i = exps[i] (or fixed_e
+// when exps is null).
+struct OzOperand {
+  const __nv_bfloat16* slices;
+  int rows;        // rows per slice (the stack's row stride between slices)
+  int ld;          // elements per row, multiple of 8
+  const int* exps;
+  int fixed_e;
+};
+int oz_beta_for(int K);          // digit width for contractions up to K terms
+int oz_slices_for(int beta);     // slices for >= 54 bits
+long long oz_max_k(int beta);    // longest exact FP32 chain for that width
+// rows [0, rows) of X into slice rows [row0, row0 + rows); per-row exponents
+// to exps[row0 + r] (or fixed_e when exps is null)
+cudaError_t oz_slice_rows(const double* X, int rows, int cols, int ldx, int S, int beta, int fixed_e,
+                          __nv_bfloat16* out, int rows_alloc, int lds, int* exps, int row0, const int* run_if,
+                          cudaStream_t s);
+// rows [r0, r1) of V as columns of the transposed slices outT[s][p][j] (fixed exponent)
+cudaError_t oz_slice_cols(const double* V, int r0, int r1, int P, int ldv, int S, int beta, int e,
+                          __nv_bfloat16* outT, int P_alloc, int ldt, cudaStream_t s);
+// C (M x N, ldc) = A B^T (or C -= A B^T) to FP64 accuracy; ws holds the
+// FP64 partials of a K split (M * N doubles per split)
+cudaError_t ozaki_gemm_nt(int M, int N, int K, const OzOperand& A, const OzOperand& B, int S, int beta, double* C,
+                          int ldc, bool subtract, double* ws, size_t ws_doubles, const int* run_if,
+                          long long spin_cap, DevStatus* st, cudaStream_t s, long long* launches);
+
 // ------------------------------------------------------ mixed-precision path
 // (lc_mixed.cu)
 // FP64 rows [r0, r1) of V -> split BF16 copies (row-major and transposed)

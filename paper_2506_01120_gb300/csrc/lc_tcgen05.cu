@@ -1442,3 +1442,463 @@ cudaError_t bracket_big(const __nv_bfloat16* Ehi, const __nv_bfloat16* Elo, long
 }
 
 }  // namespace lc
+
+// ------------------------------------------------ FP64-accurate GEMM on BF16 tensor cores
+namespace lc {
+namespace {
+
+// C (M x N, FP64) = A (M x K) B^T (B stored N x K), both operands given as
+// stacks of S slices (error-free splitting in the manner of Ozaki, Ogita,
+// Oishi and Rump): row i of an operand is x_i = 2^{e_i} sum_s 2^{-beta (s+1)}
+// d_s(i, .) with integer digits |d_s| <= 2^{beta-1}, each exact in BF16.
+// A slice product T_st = sum_k dA_s(i, k) dB_t(j, k) is a sum of integers of
+// magnitude <= 2^{2 beta - 2}; with K 2^{2 beta - 2} <= 2^24 every partial
+// sum is an integer an FP32 accumulator holds exactly, so each tcgen05.mma
+// chain over K yields T_st without rounding.  The CTA runs one such chain
+// per pair (s, t) with s + t <= S - 1 (pairs of higher level lie below
+// 2^{-beta S} of the row scales and are dropped), double-buffered in TMEM,
+// and the epilogue warps add 2^{-beta (s + t + 2)} T_st into FP64 registers
+// while the next chain runs; the row exponents 2^{e_i + e_j} are applied
+// once at the end.
+constexpr int OZ_BN = 128;
+constexpr int OZ_BK = 64;                     // one 128-byte swizzle row of BF16
+constexpr int OZ_TILE = 128 * OZ_BK * 2;      // 16 KB: 128 rows of A or of B
+constexpr int OZ_STAGE = 2 * OZ_TILE;
+constexpr int OZ_STAGES = 6;
+constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + 1024;
+constexpr int OZ_TMEM = 2 * OZ_BN;            // two 128-column FP32 accumulators
+constexpr int OZ_EPI_WARPS = 8;
+constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
+
+struct OzParams {
+  int M, N, K;
+  int a_rows, b_rows;        // rows per slice in each stack (slice s starts at row s * rows)
+  const int* eA;             // per-row exponents of A (nullptr: fA for every row)
+  const int* eB;
+  int fA, fB;
+  int S, beta, npairs;
+  int kchunk;                // k-slices of OZ_BK per K split
+  int mode;                  // 0 store, 1 subtract from C, 2 partial to ws[split][row][col]
+  double* C;
+  int ldc;
+  double* ws;
+  const int* run_if;         // device flag: 0 = skip
+  uint64_t limit_ns;
+  DevStatus* st;
+};
+
+// pair q in level order: level l = s + t holds s = 0..l
+__device__ __forceinline__ void oz_pair(int q, int* s, int* t) {
+  int l = 0;
+  while (q > l) {
+    q -= l + 1;
+    ++l;
+  }
+  *s = q;
+  *t = l - q;
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    k_ozaki_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, const OzParams p) {
+  if (p.run_if && *p.run_if == 0) return;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[OZ_STAGES], empty_bar[OZ_STAGES], t_full[2], t_empty[2], done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntn = (p.N + OZ_BN - 1) / OZ_BN, ntm = (p.M + 127) / 128;
+  const int split = blockIdx.x / (ntn * ntm);
+  const int id = blockIdx.x - split * (ntn * ntm);
+  constexpr int GROUP_M = 8;   // tile order as in k_split_gemm (operand reuse from L2)
+  const int per_group = GROUP_M * ntn;
+  const int g = id / per_group, first_m = g * GROUP_M;
+  const int gm = min(GROUP_M, ntm - first_m);
+  const int in_g = id - g * per_group;
+  const int m0 = (first_m + in_g % gm) * 128, n0 = (in_g / gm) * OZ_BN;
+  const int kt0 = split * p.kchunk;
+  const int nk = min(p.kchunk, (p.K + OZ_BK - 1) / OZ_BK - kt0);   // >= 1: the host makes every split non-empty
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < OZ_STAGES; ++q) {
+      mbar_init(&full_bar[q], 1);
+      mbar_init(&empty_bar[q], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&t_full[b], 1);
+      mbar_init(&t_empty[b], OZ_EPI_WARPS);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(OZ_TMEM)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  volatile int* ab = &abort_flag;
+
+  if (warp == 0) {
+    // ---------------- producer (lane 0): slice A_s and B_t tiles, pair by pair
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int q = 0; q < p.npairs && ok; ++q) {
+        int s, t;
+        oz_pair(q, &s, &t);
+        const int ya = s * p.a_rows + m0, yb = t * p.b_rows + n0;
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const int sg = it % OZ_STAGES;
+          if (it >= OZ_STAGES &&
+              !wait_or_abort(&empty_bar[sg], (uint32_t)(it / OZ_STAGES - 1) & 1u, p.limit_ns, ab)) {
+            record_timeout(p.st, SITE_GEMM_TMA_WAIT, it);
+            *ab = 1;
+            ok = false;
+            break;
+          }
+          uint8_t* sp = smem + sg * OZ_STAGE;
+          mbar_expect_tx(&full_bar[sg], OZ_STAGE);
+          const int kx = (kt0 + kt) * OZ_BK;
+          tma_load_2d(sp, &mA, &full_bar[sg], kx, ya);
+          tma_load_2d(sp + OZ_TILE, &mB, &full_bar[sg], kx, yb);
+        }
+      }
+      // drain: no copy may still be writing shared memory when the CTA leaves
+      for (int k = (it > OZ_STAGES ? it - OZ_STAGES : 0); k < it; ++k)
+        mbar_wait_bounded(&full_bar[k % OZ_STAGES], (uint32_t)(k / OZ_STAGES) & 1u, kDrainNs);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer (lane 0): one exact FP32 chain over K per pair
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc_bf16(128, OZ_BN);
+      int it = 0;
+      for (int q = 0; q < p.npairs; ++q) {
+        const int b = q & 1;
+        bool ok = true;
+        if (q >= 2) ok = wait_or_abort(&t_empty[b], (uint32_t)((q >> 1) - 1) & 1u, p.limit_ns, ab);
+        if (!ok) {
+          record_timeout(p.st, SITE_GEMM_MMA_WAIT, -q);
+          *ab = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(b * OZ_BN);
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const int sg = it % OZ_STAGES;
+          if (!wait_or_abort(&full_bar[sg], (uint32_t)(it / OZ_STAGES) & 1u, p.limit_ns, ab)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a = smem_u32(smem + sg * OZ_STAGE), bb = a + OZ_TILE;
+#pragma unroll
+          for (int kk = 0; kk < OZ_BK / 16; ++kk)
+            mma_bf16(d, make_sw128_desc(a + kk * 32), make_sw128_desc(bb + kk * 32), idesc, (kt | kk) ? 1u : 0u);
+          mma_commit(&empty_bar[sg]);
+        }
+        if (!ok) {
+          record_timeout(p.st, SITE_GEMM_MMA_WAIT, it);
+          *ab = 1;
+          break;
+        }
+        mma_commit(&t_full[b]);
+      }
+      mma_commit(&done_bar);   // every issued MMA has retired when this arrives
+    }
+  } else {
+    // ---------------- epilogue: warps 2-9.  Warp w reads TMEM lane quarter
+    // w % 4 (tile rows 32 (w % 4) + lane) and column half (w - 2) / 4.
+    const int qd = warp & 3, h = (warp - 2) >> 2;
+    const int r = qd * 32 + lane;
+    double acc[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) acc[i] = 0.0;
+    bool ok = true;
+    for (int q = 0; q < p.npairs; ++q) {
+      const int b = q & 1;
+      ok = __all_sync(0xffffffffu, wait_or_abort(&t_full[b], (uint32_t)(q >> 1) & 1u, p.limit_ns, ab) ? 1 : 0);
+      if (!ok) break;
+      tc_fence_after();
+      int s, t;
+      oz_pair(q, &s, &t);
+      const double w = __longlong_as_double((long long)(1023 - p.beta * (s + t + 2)) << 52);
+      const uint32_t taddr = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * OZ_BN + 64 * h);
+      float v[32];
+      tmem_ld_32cols(taddr, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) acc[i] = fma(w, (double)v[i], acc[i]);
+      tmem_ld_32cols(taddr + 32u, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) acc[32 + i] = fma(w, (double)v[i], acc[32 + i]);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&t_empty[b]);   // accumulator b may be overwritten
+    }
+    if (!ok) {
+      if (lane == 0) record_timeout(p.st, SITE_GEMM_EPI_WAIT, blockIdx.x);
+      *ab = 1;
+    } else {
+      const int row = m0 + r;
+      if (row < p.M) {
+        const int ea = p.eA ? p.eA[row] : p.fA;
+        const int cb = n0 + 64 * h;
+#pragma unroll
+        for (int i = 0; i < 64; ++i) {
+          const int col = cb + i;
+          if (col < p.N) {
+            const int eb = p.eB ? p.eB[col] : p.fB;
+            const double val = scalbn(acc[i], ea + eb);
+            if (p.mode == 0)
+              p.C[(long long)row * p.ldc + col] = val;
+            else if (p.mode == 1)
+              p.C[(long long)row * p.ldc + col] -= val;
+            else
+              p.ws[((long long)split * p.M + row) * p.N + col] = val;
+          }
+        }
+      }
+    }
+  }
+  // ---------------- teardown: every issued MMA retired before TMEM is released
+  __syncwarp();
+  if (!mbar_wait_bounded(&done_bar, 0u, p.limit_ns)) {
+    record_timeout(p.st, SITE_GEMM_EPI_WAIT, -1);
+    mbar_wait_bounded(&done_bar, 0u, kDrainNs);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM) : "memory");
+  }
+}
+
+// Split-K partials summed in split order (deterministic), stored or
+// subtracted.
+__global__ void k_oz_reduce(int M, int N, int S, const double* __restrict__ ws, double* __restrict__ C, int ldc,
+                            int subtract, const int* __restrict__ run_if) {
+  if (run_if && *run_if == 0) return;
+  const long long tot = (long long)M * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (int z = 0; z < S; ++z) t += ws[(long long)z * tot + e];
+    const long long o = (e / N) * ldc + (e % N);
+    if (subtract) C[o] -= t;
+    else C[o] = t;
+  }
+}
+
+// S balanced base-2^beta digits of y (|y| <= 1/2) to slices s of out (slice
+// stride sstride elements); each step is exact in FP64.
+__device__ __forceinline__ void oz_digits(double y, int S, double radix, __nv_bfloat16* out, long long sstride) {
+  for (int s = 0; s < S; ++s) {
+    y *= radix;
+    const double d = rint(y);
+    y -= d;
+    out[s * sstride] = __double2bfloat16(d);
+  }
+}
+
+// One warp per row of X (FP64): exponent e = ilogb(max |x|) + 2 (so that
+// |x| 2^-e < 1/2; 0 for a zero row) or the fixed exponent when exps is null,
+// then the digits of x 2^-e into slices[s][row0 + r][c].
+__global__ void k_oz_slice_rows(const double* __restrict__ X, int rows, int cols, int ldx, int S, int beta,
+                                int fixed_e, __nv_bfloat16* __restrict__ out, int rows_alloc, int lds,
+                                int* __restrict__ exps, int row0, const int* __restrict__ run_if) {
+  if (run_if && *run_if == 0) return;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  const double* x = X + (long long)r * ldx;
+  int e = fixed_e;
+  if (exps) {
+    double m = 0.0;
+    for (int c = lane; c < cols; c += 32) m = fmax(m, fabs(x[c]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    e = m > 0.0 ? ilogb(m) + 2 : 0;
+    if (lane == 0) exps[row0 + r] = e;
+  }
+  const double radix = (double)(1 << beta);
+  const long long sstride = (long long)rows_alloc * lds;
+  __nv_bfloat16* o = out + (long long)(row0 + r) * lds;
+  for (int c = lane; c < cols; c += 32) oz_digits(scalbn(x[c], -e), S, radix, o + c, sstride);
+}
+
+// Rows [r0, r1) of V (FP64) as columns r0 .. r1-1 of the transposed slices
+// outT[s][p][j] (fixed exponent), through a 32 x 32 shared-memory tile.
+__global__ void k_oz_slice_cols(const double* __restrict__ V, int r0, int r1, int P, int ldv, int S, int beta,
+                                int e, __nv_bfloat16* __restrict__ outT, int P_alloc, int ldt) {
+  __shared__ double tile[32][33];
+  const int j0 = r0 + blockIdx.y * 32, p0 = blockIdx.x * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int j = j0 + k, pp = p0 + threadIdx.x;
+    tile[k][threadIdx.x] = (j < r1 && pp < P) ? V[(long long)j * ldv + pp] : 0.0;
+  }
+  __syncthreads();
+  const double radix = (double)(1 << beta);
+  const long long sstride = (long long)P_alloc * ldt;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int pp = p0 + k, j = j0 + threadIdx.x;
+    if (pp < P && j < r1) oz_digits(scalbn(tile[threadIdx.x][k], -e), S, radix, outT + (long long)pp * ldt + j, sstride);
+  }
+}
+
+}  // namespace
+
+int oz_beta_for(int K) {
+  // largest beta <= 7 with K 2^{2 beta - 2} <= 2^24
+  int lg = 0;
+  while ((1LL << lg) < (long long)K) ++lg;
+  const int b = (26 - lg) / 2;
+  return std::max(1, std::min(7, b));
+}
+
+int oz_slices_for(int beta) { return (54 + beta - 1) / beta; }
+
+long long oz_max_k(int beta) { return 1LL << (26 - 2 * beta); }
+
+cudaError_t oz_slice_rows(const double* X, int rows, int cols, int ldx, int S, int beta, int fixed_e,
+                          __nv_bfloat16* out, int rows_alloc, int lds, int* exps, int row0, const int* run_if,
+                          cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  if (row0 < 0 || row0 + rows > rows_alloc || cols > lds || beta < 1 || beta > 7) return cudaErrorInvalidValue;
+  k_oz_slice_rows<<<(rows + 7) / 8, 256, 0, s>>>(X, rows, cols, ldx, S, beta, fixed_e, out, rows_alloc, lds, exps,
+                                                 row0, run_if);
+  return cudaGetLastError();
+}
+
+cudaError_t oz_slice_cols(const double* V, int r0, int r1, int P, int ldv, int S, int beta, int e,
+                          __nv_bfloat16* outT, int P_alloc, int ldt, cudaStream_t s) {
+  if (r1 <= r0 || P <= 0) return cudaSuccess;
+  if (P > P_alloc || r1 > ldt || beta < 1 || beta > 7) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)((P + 31) / 32), (unsigned)((r1 - r0 + 31) / 32));
+  k_oz_slice_cols<<<grid, dim3(32, 8), 0, s>>>(V, r0, r1, P, ldv, S, beta, e, outT, P_alloc, ldt);
+  return cudaGetLastError();
+}
+
+cudaError_t ozaki_gemm_nt(int M, int N, int K, const OzOperand& A, const OzOperand& B, int S, int beta, double* C,
+                          int ldc, bool subtract, double* ws, size_t ws_doubles, const int* run_if,
+                          long long spin_cap, DevStatus* st, cudaStream_t s, long long* launches) {
+  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  if (beta < 1 || beta > 7 || S < 1 || (A.ld % 8) || (B.ld % 8) || K > A.ld || K > B.ld || M > A.rows ||
+      N > B.rows)
+    return cudaErrorInvalidValue;
+  CUtensorMap mA, mB;
+  if (!make_map(&mA, A.slices, (long long)S * A.rows, K, A.ld, 128, OZ_BK) ||
+      !make_map(&mB, B.slices, (long long)S * B.rows, K, B.ld, 128, OZ_BK))
+    return cudaErrorInvalidValue;
+  const cudaError_t attr_err = smem_optin(reinterpret_cast<const void*>(k_ozaki_gemm), OZ_SMEM);
+  if (attr_err != cudaSuccess) return attr_err;
+  OzParams p;
+  p.M = M;
+  p.N = N;
+  p.K = K;
+  p.a_rows = A.rows;
+  p.b_rows = B.rows;
+  p.eA = A.exps;
+  p.eB = B.exps;
+  p.fA = A.fixed_e;
+  p.fB = B.fixed_e;
+  p.S = S;
+  p.beta = beta;
+  p.npairs = S * (S + 1) / 2;
+  p.C = C;
+  p.ldc = ldc;
+  p.ws = ws;
+  p.run_if = run_if;
+  p.limit_ns = spin_cap > 0 ? (uint64_t)spin_cap : 4000000000ull;
+  p.st = st;
+  const int nkt = (K + OZ_BK - 1) / OZ_BK;
+  const int tiles = ((M + 127) / 128) * ((N + OZ_BN - 1) / OZ_BN);
+  const int sms = device_sm_count();
+  // splits: exactness bounds each split's K; below one wave of tiles, split
+  // K further (every split keeps >= 8 k-slices) as far as the workspace holds
+  const int kmax_kt = (int)std::max<long long>(1, oz_max_k(beta) / OZ_BK);
+  int nsplit = (nkt + kmax_kt - 1) / kmax_kt;
+  if (tiles * nsplit < sms) nsplit = std::max(nsplit, std::min((sms + tiles - 1) / tiles, nkt / 8));
+  if (nsplit > 1) {
+    const size_t need = (size_t)M * N;
+    const int cap = ws ? (int)std::min<size_t>((size_t)1 << 20, ws_doubles / need) : 0;
+    const int must = (nkt + kmax_kt - 1) / kmax_kt;
+    if (must > cap && must > 1) return cudaErrorInvalidValue;   // exactness needs more than the workspace holds
+    nsplit = std::max(must, std::min(nsplit, std::max(cap, 1)));
+  }
+  int kchunk = (nkt + nsplit - 1) / nsplit;
+  kchunk = std::min(kchunk, kmax_kt);
+  nsplit = (nkt + kchunk - 1) / kchunk;              // every split non-empty
+  p.kchunk = kchunk;
+  p.mode = nsplit > 1 ? 2 : (subtract ? 1 : 0);
+  k_ozaki_gemm<<<(unsigned)(tiles * nsplit), OZ_THREADS, OZ_SMEM, s>>>(mA, mB, p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (launches) *launches += 1;
+  if (nsplit > 1) {
+    const long long tot = (long long)M * N;
+    const int grid = (int)std::min<long long>((tot + 255) / 256, (long long)sms * 8);
+    k_oz_reduce<<<grid, 256, 0, s>>>(M, N, nsplit, ws, C, ldc, subtract ? 1 : 0, run_if);
+    if (launches) *launches += 1;
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+}  // namespace lc
+
+extern "C" LC_API int lc_gemm_f64_tc(const double* A, const double* B, int M, int N, int K, double* C,
+                                     void* stream) {
+  using namespace lc;
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1) return LC_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!tcgen05_available()) return LC_ERR_CUDA;
+  // rows padded with zero digits to a multiple of the 64-wide k-box
+  const int ld = round_up(K, 64);
+  const int beta = oz_beta_for(std::min(ld, 1 << 14));
+  const int S = oz_slices_for(beta);
+  const long long kmax = oz_max_k(beta);
+  const int must = (int)((ld + kmax - 1) / kmax);
+  const size_t nA = (size_t)S * M * ld, nB = (size_t)S * N * ld;
+  // split-K partials: the splits exactness needs, or the occupancy splits of
+  // a grid below one wave (as ozaki_gemm_nt chooses them)
+  const int tiles = ((M + 127) / 128) * ((N + 127) / 128), sms = device_sm_count(), nkt = ld / 64;
+  const int occ = tiles < sms ? std::min((sms + tiles - 1) / tiles, nkt / 8) : 1;
+  const int nsplit_max = std::max(must, occ);
+  const size_t ws_doubles = nsplit_max > 1 ? (size_t)M * N * (size_t)nsplit_max : 0;
+  const size_t bytes = (nA + nB) * 2 + (size_t)(M + N) * 4 + ws_doubles * 8 + sizeof(DevStatus) + 2048;
+  char* w = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&w), bytes, s) != cudaSuccess) return LC_ERR_OOM;
+  size_t off = 0;
+  auto take = [&](size_t b) { char* p = w + off; off = (off + b + 255) & ~size_t(255); return p; };
+  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(take(nA * 2));
+  __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(take(nB * 2));
+  int* eA = reinterpret_cast<int*>(take((size_t)M * 4));
+  int* eB = reinterpret_cast<int*>(take((size_t)N * 4));
+  double* ws = reinterpret_cast<double*>(take(ws_doubles * 8));
+  DevStatus* st = reinterpret_cast<DevStatus*>(take(sizeof(DevStatus)));
+  int rc = LC_OK;
+  DevStatus hst;
+  memset(&hst, 0, sizeof(hst));
+  if (cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess ||
+      cudaMemsetAsync(As, 0, nA * 2, s) != cudaSuccess || cudaMemsetAsync(Bs, 0, nB * 2, s) != cudaSuccess)
+    rc = LC_ERR_CUDA;
+  if (rc == LC_OK && (oz_slice_rows(A, M, K, K, S, beta, 0, As, M, ld, eA, 0, nullptr, s) != cudaSuccess ||
+                      oz_slice_rows(B, N, K, K, S, beta, 0, Bs, N, ld, eB, 0, nullptr, s) != cudaSuccess))
+    rc = LC_ERR_CUDA;
+  if (rc == LC_OK) {
+    const OzOperand oa{As, M, ld, eA, 0}, ob{Bs, N, ld, eB, 0};
+    if (ozaki_gemm_nt(M, N, ld, oa, ob, S, beta, C, N, false, ws, ws_doubles, nullptr, 0, st, s, nullptr) !=
+        cudaSuccess)
+      rc = LC_ERR_CUDA;
+  }
+  if (rc == LC_OK) cudaMemcpyAsync(&hst, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(w, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && rc == LC_OK) rc = LC_ERR_CUDA;
+  if (rc == LC_OK && hst.code != 0) rc = hst.code;
+  return rc;
+}

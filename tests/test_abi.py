@@ -79,8 +79,8 @@ def test_struct_layouts_match_compiled_header(tmp_path):
 
 def test_struct_layouts_match_header():
     """ctypes mirrors of lc_options / lc_report have the C sizes."""
-    assert ctypes.sizeof(binding.Options) == 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4 + 4 + 4 + 8 + 4 + 4
-    assert ctypes.sizeof(binding.Report) == 8 * 8 + 8 * 5 + 8 + 8 + 8 + 8 + 8 * 6 + 4 * 2 + 8 * 5 + 4 * 6 + 8 + 8
+    assert ctypes.sizeof(binding.Options) == 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 4
+    assert ctypes.sizeof(binding.Report) == 8 * 8 + 8 * 5 + 8 + 8 + 8 + 8 + 8 * 6 + 4 * 2 + 8 * 5 + 4 * 6 + 8 + 8 + 8
 
 
 def test_argument_errors_need_no_gpu(built_lib):
