@@ -290,6 +290,8 @@ class Closure {
   int oz_beta_ = 0, oz_S_ = 0, oz_rows_ = 0;
   __nv_bfloat16 *Vs_ = nullptr, *VsT_ = nullptr, *Rs_ = nullptr, *Cs_ = nullptr;
   int *eR_ = nullptr, *eC_ = nullptr;
+  __nv_bfloat16* WsT_ = nullptr;      // transposed slices of one panel's accepted rows
+  int oz_w0_ = -1, oz_nw_ = -1;
   double* oz_ws_ = nullptr;
   long long oz_gemms_ = 0;
   long long scr_pass1_blocks_ = 0;    // blocks whose first projection took the screening coefficients
@@ -394,6 +396,7 @@ class Closure {
         VsT_ = ar_.take<__nv_bfloat16>((size_t)oz_S_ * ldp_ * ncap_pad_);
         Rs_ = ar_.take<__nv_bfloat16>((size_t)oz_S_ * kOzRows * ldp_);
         Cs_ = ar_.take<__nv_bfloat16>((size_t)oz_S_ * kOzRows * ncap_pad_);
+        WsT_ = ar_.take<__nv_bfloat16>((size_t)oz_S_ * ldp_ * kPanel);
         eR_ = ar_.take<int>(kOzRows);
         eC_ = ar_.take<int>(kOzRows);
         oz_ws_ = ar_.take<double>(kOzWs);
@@ -563,42 +566,57 @@ class Closure {
   // the slicing (about 2^30 multiply-adds and up)
   bool oz_use(int f, int n0) const { return oz_on_ && n0 >= 64 && (double)f * n0 * P_ >= 1073741824.0; }
 
-  // beta64 rows [0, f) = R64 rows [0, f) V[0, n0)^T
-  cudaError_t proj_coef(int f, int n0, const int* run_if = nullptr) {
-    if (!oz_use(f, n0)) {
+  // W^T slices of V rows [w0, w0 + nw) (nw <= kPanel) for the panel projections
+  cudaError_t oz_sync_w(int w0, int nw) {
+    if (w0 == oz_w0_ && nw == oz_nw_) return cudaSuccess;
+    oz_w0_ = w0;
+    oz_nw_ = nw;
+    launches_ += 1;
+    return oz_slice_cols(V64_, w0, w0 + nw, P_, ldp_, oz_S_, oz_beta_, 1, WsT_, ldp_, kPanel, s_, w0);
+  }
+
+  // beta64 rows [0, f) (row stride ncap) = rows [0, f) of R (from Rb) times
+  // V rows [w0, w0 + nw)^T
+  cudaError_t proj_coef(double* Rb, int f, int w0, int nw, const int* run_if = nullptr) {
+    if (!oz_use(f, nw)) {
       launches_ += 1;
-      return gemm_nt_f64(f, n0, P_, R64_, ldp_, V64_, ldp_, beta64_, (int)ncap_, s_, ws64_, kWs64, run_if);
+      return gemm_nt_f64(f, nw, P_, Rb, ldp_, V64_ + (size_t)w0 * ldp_, ldp_, beta64_, (int)ncap_, s_, ws64_,
+                         kWs64, run_if);
     }
-    cudaError_t e = oz_sync_v(n0);
+    cudaError_t e = oz_sync_v(w0 + nw);
+    const long long vtot = (long long)oz_S_ * ncap_pad_ - w0;    // rows from the offset base to the stack's end
     for (int r0 = 0; r0 < f && e == cudaSuccess; r0 += kOzRows) {
       const int c = std::min(kOzRows, f - r0);
-      e = oz_slice_rows(R64_ + (size_t)r0 * ldp_, c, P_, ldp_, oz_S_, oz_beta_, 0, Rs_, kOzRows, ldp_, eR_, 0,
-                        run_if, s_);
+      e = oz_slice_rows(Rb + (size_t)r0 * ldp_, c, P_, ldp_, oz_S_, oz_beta_, 0, Rs_, kOzRows, ldp_, eR_, 0, run_if,
+                        s_);
       launches_ += 1;
       if (e != cudaSuccess) break;
-      const OzOperand A{Rs_, kOzRows, ldp_, eR_, 0}, B{Vs_, ncap_pad_, ldp_, nullptr, 1};
-      e = ozaki_gemm_nt(c, n0, P_, A, B, oz_S_, oz_beta_, beta64_ + (size_t)r0 * ncap_, (int)ncap_, false, oz_ws_,
+      const OzOperand A{Rs_, kOzRows, ldp_, eR_, 0}, B{Vs_ + (size_t)w0 * ldp_, ncap_pad_, ldp_, nullptr, 1, vtot};
+      e = ozaki_gemm_nt(c, nw, P_, A, B, oz_S_, oz_beta_, beta64_ + (size_t)r0 * ncap_, (int)ncap_, false, oz_ws_,
                         kOzWs, run_if, opt.spin_cap, st_, s_, &launches_);
       oz_gemms_ += 1;
     }
     return e;
   }
-  // R64 rows [0, f) -= beta64 rows [0, f) V[0, n0)
-  cudaError_t proj_sub(int f, int n0, const int* run_if = nullptr) {
-    if (!oz_use(f, n0)) {
+  // rows [0, f) of R (from Rb) -= beta64 rows [0, f) times V rows [w0, w0 + nw)
+  cudaError_t proj_sub(double* Rb, int f, int w0, int nw, const int* run_if = nullptr) {
+    if (!oz_use(f, nw) || (w0 > 0 && nw > kPanel)) {
       launches_ += 1;
-      return gemm_nn_sub_f64(f, P_, n0, beta64_, (int)ncap_, V64_, ldp_, R64_, ldp_, s_, ws64_, kWs64, run_if);
+      return gemm_nn_sub_f64(f, P_, nw, beta64_, (int)ncap_, V64_ + (size_t)w0 * ldp_, ldp_, Rb, ldp_, s_, ws64_,
+                             kWs64, run_if);
     }
-    cudaError_t e = oz_sync_v(n0);
+    cudaError_t e = w0 == 0 ? oz_sync_v(nw) : oz_sync_w(w0, nw);
     for (int r0 = 0; r0 < f && e == cudaSuccess; r0 += kOzRows) {
       const int c = std::min(kOzRows, f - r0);
-      e = oz_slice_rows(beta64_ + (size_t)r0 * ncap_, c, n0, (int)ncap_, oz_S_, oz_beta_, 0, Cs_, kOzRows,
+      e = oz_slice_rows(beta64_ + (size_t)r0 * ncap_, c, nw, (int)ncap_, oz_S_, oz_beta_, 0, Cs_, kOzRows,
                         ncap_pad_, eC_, 0, run_if, s_);
       launches_ += 1;
       if (e != cudaSuccess) break;
-      const OzOperand A{Cs_, kOzRows, ncap_pad_, eC_, 0}, B{VsT_, ldp_, ncap_pad_, nullptr, 1};
-      e = ozaki_gemm_nt(c, P_, n0, A, B, oz_S_, oz_beta_, R64_ + (size_t)r0 * ldp_, ldp_, true, oz_ws_, kOzWs,
-                        run_if, opt.spin_cap, st_, s_, &launches_);
+      const OzOperand A{Cs_, kOzRows, ncap_pad_, eC_, 0};
+      const OzOperand B = w0 == 0 ? OzOperand{VsT_, ldp_, ncap_pad_, nullptr, 1}
+                                  : OzOperand{WsT_, ldp_, kPanel, nullptr, 1};
+      e = ozaki_gemm_nt(c, P_, nw, A, B, oz_S_, oz_beta_, Rb + (size_t)r0 * ldp_, ldp_, true, oz_ws_, kOzWs, run_if,
+                        opt.spin_cap, st_, s_, &launches_);
       oz_gemms_ += 1;
     }
     return e;
@@ -620,19 +638,19 @@ class Closure {
       // pass 1: h - V c with c the screening GEMM's coefficients (error of
       // order 1e-5 ||h||, in span(V)); pass 2 in FP64 removes what is left
       LC_TRY(gather_coef(Bhi_, Blo_, ncap_pad_, cidx_, f, n0, beta64_, (int)ncap_, s_));
-      LC_TRY(proj_sub(f, n0));
-      LC_TRY(proj_coef(f, n0));
-      LC_TRY(proj_sub(f, n0));
+      LC_TRY(proj_sub(R64_, f, 0, n0));
+      LC_TRY(proj_coef(R64_, f, 0, n0));
+      LC_TRY(proj_sub(R64_, f, 0, n0));
       LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, rnf_, s_));
       launches_ += 2;
       scr_pass1_blocks_ += 1;
     } else if (n0 > 0) {
-      LC_TRY(proj_coef(f, n0));
-      LC_TRY(proj_sub(f, n0));
+      LC_TRY(proj_coef(R64_, f, 0, n0));
+      LC_TRY(proj_sub(R64_, f, 0, n0));
       LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, rnf_, s_));
       LC_TRY(need_pass2(f, hnf_, rnf_, eta_ * eta_, tol_rel2_, tol_abs2_, need_, s_));
-      LC_TRY(proj_coef(f, n0, need_));
-      LC_TRY(proj_sub(f, n0, need_));
+      LC_TRY(proj_coef(R64_, f, 0, n0, need_));
+      LC_TRY(proj_sub(R64_, f, 0, n0, need_));
       LC_TRY(rownorm2_f64(f, P_, R64_, ldp_, rnf_, s_, need_));
       launches_ += 4;
     } else {
@@ -668,13 +686,12 @@ class Closure {
       if (a > 0) {
         const int rest = f - e0;
         double* Rr = R64_ + (size_t)e0 * ldp_;
-        const double* W = V64_ + (size_t)nb * ldp_;
         for (int pass = 0; pass < 2; ++pass) {
-          LC_TRY(gemm_nt_f64(rest, a, P_, Rr, ldp_, W, ldp_, beta64_, (int)ncap_, s_, ws64_, kWs64));
-          LC_TRY(gemm_nn_sub_f64(rest, P_, a, beta64_, (int)ncap_, W, ldp_, Rr, ldp_, s_, ws64_, kWs64));
+          LC_TRY(proj_coef(Rr, rest, (int)nb, a));
+          LC_TRY(proj_sub(Rr, rest, (int)nb, a));
         }
         LC_TRY(rownorm2_f64(rest, P_, Rr, ldp_, rnf_ + e0, s_));
-        launches_ += 5;
+        launches_ += 1;
       }
       nb = na;
     }

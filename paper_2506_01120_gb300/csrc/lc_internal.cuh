@@ -205,6 +205,7 @@ struct OzOperand {
   int ld;          // elements per row, multiple of 8
   const int* exps;
   int fixed_e;
+  long long total_rows = 0;   // rows the stack holds from `slices` on (0: S * rows)
 };
 int oz_beta_for(int K);          // digit width for contractions up to K terms
 int oz_slices_for(int beta);     // slices for >= 54 bits
@@ -214,9 +215,10 @@ long long oz_max_k(int beta);    // longest exact FP32 chain for that width
 cudaError_t oz_slice_rows(const double* X, int rows, int cols, int ldx, int S, int beta, int fixed_e,
                           __nv_bfloat16* out, int rows_alloc, int lds, int* exps, int row0, const int* run_if,
                           cudaStream_t s);
-// rows [r0, r1) of V as columns of the transposed slices outT[s][p][j] (fixed exponent)
+// rows [r0, r1) of V as columns j - jbase of the transposed slices
+// outT[s][p][j - jbase] (fixed exponent)
 cudaError_t oz_slice_cols(const double* V, int r0, int r1, int P, int ldv, int S, int beta, int e,
-                          __nv_bfloat16* outT, int P_alloc, int ldt, cudaStream_t s);
+                          __nv_bfloat16* outT, int P_alloc, int ldt, cudaStream_t s, int jbase = 0);
 // C (M x N, ldc) = A B^T (or C -= A B^T) to FP64 accuracy; ws holds the
 // FP64 partials of a K split (M * N doubles per split)
 cudaError_t ozaki_gemm_nt(int M, int N, int K, const OzOperand& A, const OzOperand& B, int S, int beta, double* C,

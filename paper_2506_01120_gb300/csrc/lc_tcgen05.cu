@@ -1476,7 +1476,11 @@ struct OzParams {
   const int* eA;             // per-row exponents of A (nullptr: fA for every row)
   const int* eB;
   int fA, fB;
-  int S, beta, npairs;
+  int S, beta;
+  // chains: a chain accumulates the pairs (s, l - s), s = s0 .. s0 + cnt - 1,
+  // of one level l in one TMEM buffer (as many as keep the FP32 sums exact)
+  int nchains;
+  signed char ch_level[64], ch_s0[64], ch_cnt[64];
   int kchunk;                // k-slices of OZ_BK per K split
   int mode;                  // 0 store, 1 subtract from C, 2 partial to ws[split][row][col]
   double* C;
@@ -1487,16 +1491,6 @@ struct OzParams {
   DevStatus* st;
 };
 
-// pair q in level order: level l = s + t holds s = 0..l
-__device__ __forceinline__ void oz_pair(int q, int* s, int* t) {
-  int l = 0;
-  while (q > l) {
-    q -= l + 1;
-    ++l;
-  }
-  *s = q;
-  *t = l - q;
-}
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_ozaki_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, const OzParams p) {
@@ -1549,9 +1543,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     if (lane == 0) {
       int it = 0;
       bool ok = true;
-      for (int q = 0; q < p.npairs && ok; ++q) {
-        int s, t;
-        oz_pair(q, &s, &t);
+      for (int q = 0; q < p.nchains && ok; ++q)
+      for (int u = 0; u < p.ch_cnt[q] && ok; ++u) {
+        const int s = p.ch_s0[q] + u, t = p.ch_level[q] - s;
         const int ya = s * p.a_rows + m0, yb = t * p.b_rows + n0;
         for (int kt = 0; kt < nk; ++kt, ++it) {
           const int sg = it % OZ_STAGES;
@@ -1578,7 +1572,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     if (lane == 0) {
       constexpr uint32_t idesc = make_idesc_bf16(128, OZ_BN);
       int it = 0;
-      for (int q = 0; q < p.npairs; ++q) {
+      for (int q = 0; q < p.nchains; ++q) {
         const int b = q & 1;
         bool ok = true;
         if (q >= 2) ok = wait_or_abort(&t_empty[b], (uint32_t)((q >> 1) - 1) & 1u, p.limit_ns, ab);
@@ -1589,6 +1583,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         }
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(b * OZ_BN);
+        for (int u = 0; u < p.ch_cnt[q] && ok; ++u)
         for (int kt = 0; kt < nk; ++kt, ++it) {
           const int sg = it % OZ_STAGES;
           if (!wait_or_abort(&full_bar[sg], (uint32_t)(it / OZ_STAGES) & 1u, p.limit_ns, ab)) {
@@ -1599,7 +1594,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           const uint32_t a = smem_u32(smem + sg * OZ_STAGE), bb = a + OZ_TILE;
 #pragma unroll
           for (int kk = 0; kk < OZ_BK / 16; ++kk)
-            mma_bf16(d, make_sw128_desc(a + kk * 32), make_sw128_desc(bb + kk * 32), idesc, (kt | kk) ? 1u : 0u);
+            mma_bf16(d, make_sw128_desc(a + kk * 32), make_sw128_desc(bb + kk * 32), idesc,
+                     (u | kt | kk) ? 1u : 0u);
           mma_commit(&empty_bar[sg]);
         }
         if (!ok) {
@@ -1620,14 +1616,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
     for (int i = 0; i < 64; ++i) acc[i] = 0.0;
     bool ok = true;
-    for (int q = 0; q < p.npairs; ++q) {
+    for (int q = 0; q < p.nchains; ++q) {
       const int b = q & 1;
       ok = __all_sync(0xffffffffu, wait_or_abort(&t_full[b], (uint32_t)(q >> 1) & 1u, p.limit_ns, ab) ? 1 : 0);
       if (!ok) break;
       tc_fence_after();
-      int s, t;
-      oz_pair(q, &s, &t);
-      const double w = __longlong_as_double((long long)(1023 - p.beta * (s + t + 2)) << 52);
+      const double w = __longlong_as_double((long long)(1023 - p.beta * (p.ch_level[q] + 2)) << 52);
       const uint32_t taddr = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * OZ_BN + 64 * h);
       float v[32];
       tmem_ld_32cols(taddr, v);
@@ -1695,20 +1689,47 @@ __global__ void k_oz_reduce(int M, int N, int S, const double* __restrict__ ws, 
   }
 }
 
-// S balanced base-2^beta digits of y (|y| <= 1/2) to slices s of out (slice
-// stride sstride elements); each step is exact in FP64.
-__device__ __forceinline__ void oz_digits(double y, int S, double radix, __nv_bfloat16* out, long long sstride) {
-  for (int s = 0; s < S; ++s) {
-    y *= radix;
-    const double d = rint(y);
-    y -= d;
-    out[s * sstride] = __double2bfloat16(d);
-  }
+// The slicing runs on the integer pipes (FP64 is the slowest pipe of the
+// part): x 2^shift rounded to the nearest integer, from x's bits.  Zero and
+// subnormal inputs give 0 (they lie far below any digit kept).
+__device__ __forceinline__ long long oz_fixed(double x, int shift) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0) return 0;
+  const long long m = (b & ((1LL << 52) - 1)) | (1LL << 52);   // |x| = m 2^(ex - 1075)
+  const int sh = ex - 1075 + shift;
+  long long v;
+  if (sh >= 0) v = m << sh;                     // callers keep |x 2^shift| <= 2^55
+  else if (sh < -53) v = 0;                     // below 1/2
+  else v = (m + (1LL << (-sh - 1))) >> (-sh);   // round half up
+  return b < 0 ? -v : v;
 }
 
-// One warp per row of X (FP64): exponent e = ilogb(max |x|) + 2 (so that
-// |x| 2^-e < 1/2; 0 for a zero row) or the fixed exponent when exps is null,
-// then the digits of x 2^-e into slices[s][row0 + r][c].
+// S balanced base-2^beta digits of Y = round(x 2^(beta S - e)), |Y| <=
+// 2^(beta S - 1): from the least significant, d = Y mod 2^beta in
+// [-2^(beta-1), 2^(beta-1)), Y = (Y - d) / 2^beta; the top digit is what
+// is left, within 2^(beta-1) in magnitude (it may equal +-2^(beta-1)).  Slice s (weight 2^(-beta (s+1))) at
+// out[s * sstride].
+__device__ __forceinline__ void oz_digits(double x, int e, int S, int beta, __nv_bfloat16* out, long long sstride) {
+  long long Y = oz_fixed(x, beta * S - e);
+  const long long half = 1LL << (beta - 1), mask = (1LL << beta) - 1;
+  for (int s = S - 1; s >= 1; --s) {
+    const long long d = ((Y + half) & mask) - half;
+    Y = (Y - d) >> beta;
+    out[s * sstride] = __float2bfloat16_rn((float)d);
+  }
+  out[0] = __float2bfloat16_rn((float)Y);   // the rest, |Y| <= 2^(beta-1)
+}
+
+// exponent e with |x| 2^-e < 1/2 for the largest |x| of a row, from the bits
+// of max |x| (non-negative doubles order as their bit patterns); 0 for a zero row
+__device__ __forceinline__ int oz_row_exp(long long maxbits) {
+  const int ex = (int)((maxbits >> 52) & 0x7FF);
+  return ex == 0 ? 0 : ex - 1023 + 2;
+}
+
+// One warp per row of X (FP64): per-row exponent (or the fixed one when
+// exps is null), then the digits into slices[s][row0 + r][c].
 __global__ void k_oz_slice_rows(const double* __restrict__ X, int rows, int cols, int ldx, int S, int beta,
                                 int fixed_e, __nv_bfloat16* __restrict__ out, int rows_alloc, int lds,
                                 int* __restrict__ exps, int row0, const int* __restrict__ run_if) {
@@ -1719,22 +1740,21 @@ __global__ void k_oz_slice_rows(const double* __restrict__ X, int rows, int cols
   const double* x = X + (long long)r * ldx;
   int e = fixed_e;
   if (exps) {
-    double m = 0.0;
-    for (int c = lane; c < cols; c += 32) m = fmax(m, fabs(x[c]));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    e = m > 0.0 ? ilogb(m) + 2 : 0;
+    long long m = 0;
+    for (int c = lane; c < cols; c += 32) m = max(m, __double_as_longlong(x[c]) & 0x7FFFFFFFFFFFFFFFLL);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    e = oz_row_exp(m);
     if (lane == 0) exps[row0 + r] = e;
   }
-  const double radix = (double)(1 << beta);
   const long long sstride = (long long)rows_alloc * lds;
   __nv_bfloat16* o = out + (long long)(row0 + r) * lds;
-  for (int c = lane; c < cols; c += 32) oz_digits(scalbn(x[c], -e), S, radix, o + c, sstride);
+  for (int c = lane; c < cols; c += 32) oz_digits(x[c], e, S, beta, o + c, sstride);
 }
 
-// Rows [r0, r1) of V (FP64) as columns r0 .. r1-1 of the transposed slices
-// outT[s][p][j] (fixed exponent), through a 32 x 32 shared-memory tile.
+// Rows [r0, r1) of V (FP64) as columns j - jbase of the transposed slices
+// outT[s][p][j - jbase] (fixed exponent), through a 32 x 32 shared-memory tile.
 __global__ void k_oz_slice_cols(const double* __restrict__ V, int r0, int r1, int P, int ldv, int S, int beta,
-                                int e, __nv_bfloat16* __restrict__ outT, int P_alloc, int ldt) {
+                                int e, __nv_bfloat16* __restrict__ outT, int P_alloc, int ldt, int jbase) {
   __shared__ double tile[32][33];
   const int j0 = r0 + blockIdx.y * 32, p0 = blockIdx.x * 32;
   for (int k = threadIdx.y; k < 32; k += blockDim.y) {
@@ -1742,11 +1762,10 @@ __global__ void k_oz_slice_cols(const double* __restrict__ V, int r0, int r1, in
     tile[k][threadIdx.x] = (j < r1 && pp < P) ? V[(long long)j * ldv + pp] : 0.0;
   }
   __syncthreads();
-  const double radix = (double)(1 << beta);
   const long long sstride = (long long)P_alloc * ldt;
   for (int k = threadIdx.y; k < 32; k += blockDim.y) {
     const int pp = p0 + k, j = j0 + threadIdx.x;
-    if (pp < P && j < r1) oz_digits(scalbn(tile[threadIdx.x][k], -e), S, radix, outT + (long long)pp * ldt + j, sstride);
+    if (pp < P && j < r1) oz_digits(tile[threadIdx.x][k], e, S, beta, outT + (long long)pp * ldt + (j - jbase), sstride);
   }
 }
 
@@ -1775,11 +1794,12 @@ cudaError_t oz_slice_rows(const double* X, int rows, int cols, int ldx, int S, i
 }
 
 cudaError_t oz_slice_cols(const double* V, int r0, int r1, int P, int ldv, int S, int beta, int e,
-                          __nv_bfloat16* outT, int P_alloc, int ldt, cudaStream_t s) {
+                          __nv_bfloat16* outT, int P_alloc, int ldt, cudaStream_t s, int jbase) {
   if (r1 <= r0 || P <= 0) return cudaSuccess;
-  if (P > P_alloc || r1 > ldt || beta < 1 || beta > 7) return cudaErrorInvalidValue;
+  if (P > P_alloc || jbase < 0 || jbase > r0 || r1 - jbase > ldt || beta < 1 || beta > 7)
+    return cudaErrorInvalidValue;
   dim3 grid((unsigned)((P + 31) / 32), (unsigned)((r1 - r0 + 31) / 32));
-  k_oz_slice_cols<<<grid, dim3(32, 8), 0, s>>>(V, r0, r1, P, ldv, S, beta, e, outT, P_alloc, ldt);
+  k_oz_slice_cols<<<grid, dim3(32, 8), 0, s>>>(V, r0, r1, P, ldv, S, beta, e, outT, P_alloc, ldt, jbase);
   return cudaGetLastError();
 }
 
@@ -1791,8 +1811,9 @@ cudaError_t ozaki_gemm_nt(int M, int N, int K, const OzOperand& A, const OzOpera
       N > B.rows)
     return cudaErrorInvalidValue;
   CUtensorMap mA, mB;
-  if (!make_map(&mA, A.slices, (long long)S * A.rows, K, A.ld, 128, OZ_BK) ||
-      !make_map(&mB, B.slices, (long long)S * B.rows, K, B.ld, 128, OZ_BK))
+  const long long ta = A.total_rows > 0 ? A.total_rows : (long long)S * A.rows;
+  const long long tb = B.total_rows > 0 ? B.total_rows : (long long)S * B.rows;
+  if (!make_map(&mA, A.slices, ta, K, A.ld, 128, OZ_BK) || !make_map(&mB, B.slices, tb, K, B.ld, 128, OZ_BK))
     return cudaErrorInvalidValue;
   const cudaError_t attr_err = smem_optin(reinterpret_cast<const void*>(k_ozaki_gemm), OZ_SMEM);
   if (attr_err != cudaSuccess) return attr_err;
@@ -1808,7 +1829,6 @@ cudaError_t ozaki_gemm_nt(int M, int N, int K, const OzOperand& A, const OzOpera
   p.fB = B.fixed_e;
   p.S = S;
   p.beta = beta;
-  p.npairs = S * (S + 1) / 2;
   p.C = C;
   p.ldc = ldc;
   p.ws = ws;
@@ -1835,6 +1855,18 @@ cudaError_t ozaki_gemm_nt(int M, int N, int K, const OzOperand& A, const OzOpera
   nsplit = (nkt + kchunk - 1) / kchunk;              // every split non-empty
   p.kchunk = kchunk;
   p.mode = nsplit > 1 ? 2 : (subtract ? 1 : 0);
+  // chains: up to g pairs of a level share an accumulator while
+  // g (kchunk OZ_BK) 2^(2 beta - 2) <= 2^24
+  const int g = (int)std::max<long long>(1, oz_max_k(beta) / ((long long)kchunk * OZ_BK));
+  p.nchains = 0;
+  for (int l = 0; l < S; ++l)
+    for (int s0 = 0; s0 <= l; s0 += g) {
+      if (p.nchains >= 64) return cudaErrorInvalidValue;
+      p.ch_level[p.nchains] = (signed char)l;
+      p.ch_s0[p.nchains] = (signed char)s0;
+      p.ch_cnt[p.nchains] = (signed char)std::min(g, l + 1 - s0);
+      ++p.nchains;
+    }
   k_ozaki_gemm<<<(unsigned)(tiles * nsplit), OZ_THREADS, OZ_SMEM, s>>>(mA, mB, p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -108,3 +108,16 @@ def test_su64_chain_and_su128_growth_with_tc_projections():
     assert r.dim == 16383
     assert r.report["accept_tc_gemms"] > 0
     assert r.report["ortho_defect"] < 1e-12
+
+
+def test_su128_prefix_panel_projections_match_fp64_gemms():
+    """su(128) random pair, first 12000 candidates (growth blocks of 1024 with
+    hundreds of accepts each, decided in panels of 128 rows): with the
+    tensor-core projections, including those of each panel's accepts out of
+    the later rows, the basis equals the FP64-SIMT-GEMM run's."""
+    g, _ = inputs.workload_generators("su128_random2_d128")
+    a = binding.lie_closure(g, 1e-8, precision="mixed", max_candidates=12000, max_dim=16384)
+    b = binding.lie_closure(g, 1e-8, precision="mixed", max_candidates=12000, max_dim=16384, accept_gemm=1)
+    assert a.report["accept_tc_gemms"] > 0 and b.report["accept_tc_gemms"] == 0
+    assert a.dim == b.dim > 1000
+    np.testing.assert_allclose(a.basis, b.basis, atol=1e-11, rtol=0)
