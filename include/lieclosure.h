@@ -132,9 +132,12 @@ typedef struct {
   int accept_kernel;          /* in-block test and append: 0 = by shape
                                  (default), 1 = one CTA per flagged row,
                                  2 = every row sliced across all SMs (panels of
-                                 at most 128 rows).  Both take the same
-                                 decisions in the same order and differ only in
-                                 the order of the FP64 partial sums */
+                                 at most 128 rows), 3 = one CTA per flagged
+                                 row holding it in shared memory (rows of at
+                                 most 25,600 components; else 1).  All take
+                                 the same decisions in the same order; 1 and 3
+                                 compute identical values, 2 differs in the
+                                 order of the FP64 partial sums */
   int fp64_first_pass;        /* mixed mode: nonzero = the first projection of
                                  flagged candidates is always an FP64 GEMM.
                                  Default 0: when some flagged row of a block

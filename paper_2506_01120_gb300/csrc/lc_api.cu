@@ -1073,7 +1073,7 @@ int check_args(const void* g, int k, int d, double tol, long long max_dim, const
       o.screen_kappa < 0 || !(o.screen_kappa == o.screen_kappa))
     return LC_ERR_ARG;
   if (o.tol_mode != LC_TOL_RELATIVE && o.tol_mode != LC_TOL_ABSOLUTE) return LC_ERR_ARG;
-  if (o.accept_kernel < 0 || o.accept_kernel > 2) return LC_ERR_ARG;
+  if (o.accept_kernel < 0 || o.accept_kernel > 3) return LC_ERR_ARG;
   if (o.accept_gemm < 0 || o.accept_gemm > 1) return LC_ERR_ARG;
   if ((long long)d * d > (1ll << 31) / 2) return LC_ERR_ARG;
   return LC_OK;

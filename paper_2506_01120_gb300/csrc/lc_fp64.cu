@@ -784,6 +784,103 @@ __global__ void __launch_bounds__(256) k_accept_wide(int f, double* __restrict__
   }
 }
 
+// The in-block test and append with each later row held in shared memory
+// by the CTA that owns it (CTA j owns row j; f <= co-resident CTAs, P
+// doubles of dynamic shared memory each).  Per accept only the pivot row
+// r_i streams from L2; the owner of row j runs three sweeps over its row:
+// <r_i, r_j>; r_j -= c1 r_i fused with the second pass's <r_i, r_j>;
+// r_j -= c2 r_i fused with ||r_j||^2 and the write-back of r_j (a later
+// pivot is read from global memory).  Per component and per partial sum
+// this is k_accept_seq's arithmetic in k_accept_seq's order; one bounded
+// grid barrier per accept.  The pivot's owner appends it to V.
+__global__ void __launch_bounds__(256, 1) k_accept_rowsmem(int f, double* __restrict__ R, int ldr,
+                                                           double* __restrict__ rn2, const double* __restrict__ hn2,
+                                                           double tol_rel2, double tol_abs2, double eta2,
+                                                           double* __restrict__ V, int ldv, int ncap, int P,
+                                                           DevStats* stats, DevStatus* st, unsigned int* bar,
+                                                           uint64_t limit_ns, int phantom,
+                                                           const double* __restrict__ Hraw, double* __restrict__ Bk,
+                                                           double* __restrict__ bn2,
+                                                           const float* __restrict__ rho2_screen) {
+  extern __shared__ double row[];
+  __shared__ double red[33];
+  __shared__ int ok_smem;
+  const unsigned int Gb = gridDim.x + (unsigned)phantom;   // phantom (test hook): an arrival that never comes
+  const int j = blockIdx.x;
+  double* rj = R + (long long)j * ldr;
+  const int slot0 = stats->ncur;   // CTA 0 writes it back only after every CTA passed a barrier
+  for (int p = threadIdx.x; p < P; p += blockDim.x) row[p] = rj[p];
+  __syncthreads();
+  int nacc = 0, nbar = 0;
+  for (int i = 0; i < f; ++i) {
+    const double h2 = hn2[i];
+    const double r2 = __ldcg(&rn2[i]);
+    const bool nonzero = h2 > eta2;
+    if (!(nonzero && r2 > tol_rel2 * h2 + tol_abs2)) {
+      if (j == 0 && threadIdx.x == 0 && nonzero) atomicMax(&stats->max_rej_bits, dbits(sqrt(r2 / h2)));
+      continue;
+    }
+    const int slot = slot0 + nacc;
+    if (slot >= ncap) {   // the same test in every CTA
+      if (j == 0 && threadIdx.x == 0 && atomicCAS(&st->code, 0, (int)LC_ERR_CAPACITY) == 0) {
+        st->where = SITE_ACCEPT_CAPACITY;
+        st->info = i;
+      }
+      break;
+    }
+    ++nacc;
+    const double inv = 1.0 / sqrt(r2);
+    if (j == i) {
+      double* v = V + (long long)slot * ldv;
+      for (int p = threadIdx.x; p < P; p += blockDim.x) v[p] = row[p] * inv;
+      if (Bk) {   // Algorithm 3: the bracket itself joins B
+        const double* hr = Hraw + (long long)i * ldr;
+        double* b = Bk + (long long)slot * ldv;
+        for (int p = threadIdx.x; p < P; p += blockDim.x) b[p] = hr[p];
+      }
+      if (threadIdx.x == 0) {
+        atomicMin(&stats->min_acc_bits, dbits(sqrt(r2 / h2)));
+        if (rho2_screen) atomicMin(&stats->min_acc_screen_bits, dbits(sqrt((double)rho2_screen[i])));
+        if (Bk) bn2[slot] = h2;
+      }
+    } else if (j > i) {
+      const double* ri = R + (long long)i * ldr;
+      double s = 0.0;
+      for (int p = threadIdx.x; p < P; p += blockDim.x) s = fma(__ldcg(&ri[p]), row[p], s);
+      const double c1 = block_sum(s, red) * inv * inv;   // as k_accept_seq associates it
+      s = 0.0;
+      for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        const double x = __ldcg(&ri[p]);
+        const double y = fma(-c1, x, row[p]);
+        row[p] = y;
+        s = fma(x, y, s);
+      }
+      const double c2 = block_sum(s, red) * inv * inv;
+      s = 0.0;
+      for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        const double x = __ldcg(&ri[p]);
+        const double y = fma(-c2, x, row[p]);
+        row[p] = y;
+        __stcg(&rj[p], y);
+        s = fma(y, y, s);
+      }
+      s = block_sum(s, red);
+      if (threadIdx.x == 0) __stcg(&rn2[j], s);
+    }
+    if (i + 1 < f) {
+      ++nbar;
+      if (!grid_barrier(bar, bar + 1, Gb, limit_ns, st, &ok_smem)) return;
+    }
+  }
+  if (nacc > 0 && nbar == 0) {   // every CTA must have read ncur before it changes
+    if (!grid_barrier(bar, bar + 1, Gb, limit_ns, st, &ok_smem)) return;
+  }
+  if (j == 0 && threadIdx.x == 0) {
+    stats->ncur = slot0 + nacc;
+    stats->naccepted += nacc;
+  }
+}
+
 // Second Gram-Schmidt pass needed?  After one FP64 pass the loss of
 // orthogonality of r is about eps ||h|| / ||r||; when ||r|| >= ||h|| / sqrt(2)
 // for every row (or the row is certainly dependent, ||r|| <= tol ||h|| / 2)
@@ -1076,11 +1173,23 @@ size_t accept_wide_part_doubles() { return (size_t)3 * kAcceptWideMaxRows * (siz
 // when f is small; slicing the rows costs three grid barriers and
 // 3 ceil((f - i - 1) / 8) CTA reductions per accept, which pay off once the
 // rows are long.
+// rows held in shared memory: one CTA per flagged row, all co-resident
+static bool accept_rowsmem_fits(int f, int P) {
+  if ((size_t)P * sizeof(double) > kAcceptRowSmemMax) return false;
+  const int bytes = P * (int)sizeof(double);
+  if (smem_optin((const void*)k_accept_rowsmem, bytes) != cudaSuccess) return false;
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_accept_rowsmem, 256, bytes) != cudaSuccess) return false;
+  return f <= per * device_sm_count();
+}
+
 int accept_kernel_for(int f, int P, int requested) {
   if (f > kAcceptWideMaxRows) return 1;
+  if (requested == 3) return accept_rowsmem_fits(f, P) ? 3 : 1;
   if (requested == 1 || requested == 2) return requested;
   if (P >= (1 << 18)) return 2;
   if (P >= (1 << 16) && f <= 32) return 2;
+  if (accept_rowsmem_fits(f, P)) return 3;
   return 1;
 }
 
@@ -1097,6 +1206,14 @@ cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2
                     &V,    &ldv, &ncap, &P,    &stats,      &st,       &bar,               &lim,
                     &phantom, (void*)&Hraw, &Bk, &bn2, (void*)&rho2_screen, &wpart};
     return cudaLaunchCooperativeKernel((const void*)k_accept_wide, dim3(G), dim3(256), args, 0, s);
+  }
+  if (kernel == 3) {
+    if (!accept_rowsmem_fits(f, P)) return cudaErrorInvalidValue;
+    void* args[] = {&f,     &R,   &ldr, &rn2, (void*)&hn2, &tol_rel2,    &tol_abs2, &eta2, &V,   &ldv,
+                    &ncap,  &P,   &stats, &st, &bar,       &lim,         &phantom,  (void*)&Hraw, &Bk, &bn2,
+                    (void*)&rho2_screen};
+    return cudaLaunchCooperativeKernel((const void*)k_accept_rowsmem, dim3(f), dim3(256), args,
+                                       (size_t)P * sizeof(double), s);
   }
   const int nblocks = coresident_ctas((const void*)k_accept_seq, 0);
   if (nblocks <= 0) return cudaErrorInvalidDevice;

@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 #include <cstddef>
+#include <map>
 #include <mutex>
 #include <set>
 #include <utility>
@@ -74,19 +75,23 @@ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 inline long long round_up_ll(long long x, long long m) { return (x + m - 1) / m * m; }
 
 // Dynamic shared memory above 48 KB is an opt-in attribute of a kernel in
-// one device's context, so it is set once per (kernel, device, size) with the
-// device current, not once per process.
+// one device's context (the launch limit for that kernel), so it is raised
+// per (kernel, device) with the device current, never lowered: a kernel
+// launched with several sizes keeps the largest limit asked for.  Up to the
+// default 48 KB nothing is set.
 inline cudaError_t smem_optin(const void* kernel, int bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
   static std::mutex mu;
-  static std::set<std::pair<std::pair<const void*, int>, int>> done;
+  static std::map<std::pair<const void*, int>, int> limit;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> g(mu);
-  const auto key = std::make_pair(std::make_pair(kernel, dev), bytes);
-  if (done.count(key)) return cudaSuccess;
+  const auto key = std::make_pair(kernel, dev);
+  auto it = limit.find(key);
+  if (it != limit.end() && it->second >= bytes) return cudaSuccess;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) done.insert(key);
+  if (e == cudaSuccess) limit[key] = bytes;
   return e;
 }
 
@@ -159,8 +164,11 @@ cudaError_t rownorm2_f64(int M, int N, const double* A, int lda, double* out, cu
 // rho2_screen (optional): the rows' screened relative residuals squared.
 // kernel: 1 = one CTA per row (k_accept_seq), 2 = every row sliced across the
 // grid (k_accept_wide; f <= kAcceptWideMaxRows, wpart holds
-// accept_wide_part_doubles() doubles), 0 = by shape
+// accept_wide_part_doubles() doubles), 3 = one CTA per row with the row in
+// shared memory (k_accept_rowsmem; P doubles <= kAcceptRowSmemMax bytes, f
+// co-resident CTAs), 0 = by shape
 constexpr int kAcceptWideMaxRows = 128;
+constexpr size_t kAcceptRowSmemMax = 200 * 1024;
 size_t accept_wide_part_doubles();
 int accept_kernel_for(int f, int P, int requested);
 cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2, double tol_rel2, double tol_abs2,

@@ -106,7 +106,7 @@ def test_sliced_accept_timeout_is_reported_and_device_stays_usable():
 
 def test_bad_accept_kernel_is_an_argument_error():
     g = inputs.generators_from_labels(inputs.su2n_chain_labels(2))
-    r = binding.lie_closure(g, 1e-10, accept_kernel=3, check=False)
+    r = binding.lie_closure(g, 1e-10, accept_kernel=4, check=False)
     assert r.status == binding.LC_ERR_ARG
 
 
@@ -165,3 +165,40 @@ def test_fp64_mode_never_takes_screen_coefficients():
     g, tol, ncand = _case("rand_d16_prefix")
     r = binding.lie_closure(g, tol, precision="fp64", max_candidates=ncand)
     assert r.report["screen_pass1_blocks"] == 0
+
+
+# ------------------------------------------------ rows held in shared memory
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", ["so6", "rand_d8", "rand_d16_prefix", "rand_d6_k3"])
+def test_rowsmem_accept_identical_to_row_per_cta(prec, name):
+    """accept_kernel = 3 (each later row kept in its CTA's shared memory,
+    fused sweeps) computes k_accept_seq's values in k_accept_seq's order:
+    the basis is bit-identical to accept_kernel = 1's and equals the
+    oracle's."""
+    g, tol, ncand = _case(name)
+    kw = {} if ncand is None else {"max_candidates": ncand}
+    a = binding.lie_closure(g, tol, precision=prec, accept_kernel=3, **kw)
+    b = binding.lie_closure(g, tol, precision=prec, accept_kernel=1, **kw)
+    assert a.dim == b.dim
+    np.testing.assert_array_equal(a.basis, b.basis)
+    ref = oc.alg4_orthonormalization(g, tol, **kw)
+    assert a.dim == ref.dim
+    np.testing.assert_allclose(a.basis, ref.basis, atol=1e-11, rtol=0)
+
+
+def test_rowsmem_accept_alg3_capacity_and_timeout():
+    g, tol = inputs.generators_from_labels(inputs.su2n_chain_labels(3)), 1e-10
+    ref = oc.alg3_orthonormalization(g, tol)
+    B, V, st, rep = binding.lie_closure_alg3(g, tol, precision="mixed", accept_kernel=3)
+    assert st == binding.LC_OK and B.shape[0] == ref.dim
+    np.testing.assert_allclose(V, ref.V, atol=1e-11)
+    g4 = inputs.random_set(4, 2, seed=5)
+    ref4 = oc.alg4_orthonormalization(g4, 1e-8)
+    r = binding.lie_closure(g4, 1e-8, max_dim=10, check=False, precision="mixed", accept_kernel=3)
+    assert r.status == binding.LC_ERR_CAPACITY and r.dim == 10
+    np.testing.assert_allclose(r.basis, ref4.basis[:10], atol=1e-12)
+    r = binding.lie_closure(g, 1e-10, precision="mixed", fault_inject=1, spin_cap=50_000_000, check=False,
+                            accept_kernel=3)
+    assert r.status == binding.LC_ERR_TIMEOUT
+    ok = binding.lie_closure(g, 1e-10, precision="mixed", accept_kernel=3)
+    assert ok.status == binding.LC_OK and ok.dim == 63
