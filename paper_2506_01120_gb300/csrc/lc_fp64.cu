@@ -488,6 +488,12 @@ __global__ void __launch_bounds__(kCmpThreads) k_screen_pass2(const T* __restric
   }
 }
 
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The
 // wait is bounded: after limit_ns the CTA records LC_ERR_TIMEOUT and returns
 // false, and the caller leaves the kernel.
@@ -496,7 +502,7 @@ __device__ bool grid_barrier(unsigned int* count, unsigned int* gen, unsigned in
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned int g0 = atomicAdd(gen, 0u);
+    const unsigned int g0 = ld_acquire_u32(gen);
     __threadfence();
     const unsigned int arrived = atomicAdd(count, 1u);
     if (arrived == nblocks - 1) {
@@ -506,8 +512,10 @@ __device__ bool grid_barrier(unsigned int* count, unsigned int* gen, unsigned in
     } else {
       uint64_t t0;
       asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t0));
+      // poll with plain acquire loads (an atomic per poll from every waiting
+      // SM would queue at the counter's L2 slice ahead of the last arrival)
       for (unsigned int it = 0;; ++it) {
-        if (atomicAdd(gen, 0u) != g0) break;
+        if (ld_acquire_u32(gen) != g0) break;
         if ((it & 63u) == 63u) {
           uint64_t t;
           asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -573,10 +581,12 @@ __global__ void __launch_bounds__(256) k_accept_seq(int f, double* __restrict__ 
       __syncthreads();
       if (slot >= 0) {
         double* v = V + (long long)slot * ldv;
+        #pragma unroll 8
         for (int p = threadIdx.x; p < P; p += blockDim.x) v[p] = __ldcg(&ri[p]) * inv;
         if (Bk) {   // Algorithm 3: the bracket itself joins B
           const double* hr = Hraw + (long long)i * ldr;
           double* b = Bk + (long long)slot * ldv;
+          #pragma unroll 8
           for (int p = threadIdx.x; p < P; p += blockDim.x) b[p] = hr[p];
           if (threadIdx.x == 0) bn2[slot] = h2;
         }
@@ -586,11 +596,14 @@ __global__ void __launch_bounds__(256) k_accept_seq(int f, double* __restrict__ 
       double* rj = R + (long long)j * ldr;
       for (int pass = 0; pass < 2; ++pass) {
         double sacc = 0.0;
+        #pragma unroll 8
         for (int p = threadIdx.x; p < P; p += blockDim.x) sacc = fma(__ldcg(&ri[p]), rj[p], sacc);
         const double c = block_sum(sacc, red) * inv * inv;
+        #pragma unroll 8
         for (int p = threadIdx.x; p < P; p += blockDim.x) rj[p] = fma(-c, __ldcg(&ri[p]), rj[p]);
       }
       double sacc = 0.0;
+      #pragma unroll 8
       for (int p = threadIdx.x; p < P; p += blockDim.x) sacc = fma(rj[p], rj[p], sacc);
       sacc = block_sum(sacc, red);
       if (threadIdx.x == 0) rn2[j] = sacc;
@@ -793,6 +806,8 @@ __global__ void __launch_bounds__(256) k_accept_wide(int f, double* __restrict__
 // pivot is read from global memory).  Per component and per partial sum
 // this is k_accept_seq's arithmetic in k_accept_seq's order; one bounded
 // grid barrier per accept.  The pivot's owner appends it to V.
+constexpr int kSweepBatch = 8;
+
 __global__ void __launch_bounds__(256, 1) k_accept_rowsmem(int f, double* __restrict__ R, int ldr,
                                                            double* __restrict__ rn2, const double* __restrict__ hn2,
                                                            double tol_rel2, double tol_abs2, double eta2,
@@ -809,6 +824,7 @@ __global__ void __launch_bounds__(256, 1) k_accept_rowsmem(int f, double* __rest
   const int j = blockIdx.x;
   double* rj = R + (long long)j * ldr;
   const int slot0 = stats->ncur;   // CTA 0 writes it back only after every CTA passed a barrier
+  #pragma unroll 8
   for (int p = threadIdx.x; p < P; p += blockDim.x) row[p] = rj[p];
   __syncthreads();
   int nacc = 0, nbar = 0;
@@ -832,10 +848,12 @@ __global__ void __launch_bounds__(256, 1) k_accept_rowsmem(int f, double* __rest
     const double inv = 1.0 / sqrt(r2);
     if (j == i) {
       double* v = V + (long long)slot * ldv;
+      #pragma unroll 8
       for (int p = threadIdx.x; p < P; p += blockDim.x) v[p] = row[p] * inv;
       if (Bk) {   // Algorithm 3: the bracket itself joins B
         const double* hr = Hraw + (long long)i * ldr;
         double* b = Bk + (long long)slot * ldv;
+        #pragma unroll 8
         for (int p = threadIdx.x; p < P; p += blockDim.x) b[p] = hr[p];
       }
       if (threadIdx.x == 0) {
@@ -844,25 +862,62 @@ __global__ void __launch_bounds__(256, 1) k_accept_rowsmem(int f, double* __rest
         if (Bk) bn2[slot] = h2;
       }
     } else if (j > i) {
+      // each sweep loads the pivot in batches of kSweepBatch per thread
+      // ahead of the arithmetic (same per-thread order of p as a strided loop)
       const double* ri = R + (long long)i * ldr;
+      const int step = kSweepBatch * blockDim.x;
       double s = 0.0;
-      for (int p = threadIdx.x; p < P; p += blockDim.x) s = fma(__ldcg(&ri[p]), row[p], s);
+      for (int p0 = threadIdx.x; p0 < P; p0 += step) {
+        double x[kSweepBatch];
+#pragma unroll
+        for (int u = 0; u < kSweepBatch; ++u) {
+          const int p = p0 + u * blockDim.x;
+          x[u] = p < P ? __ldcg(&ri[p]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kSweepBatch; ++u) {
+          const int p = p0 + u * blockDim.x;
+          if (p < P) s = fma(x[u], row[p], s);
+        }
+      }
       const double c1 = block_sum(s, red) * inv * inv;   // as k_accept_seq associates it
       s = 0.0;
-      for (int p = threadIdx.x; p < P; p += blockDim.x) {
-        const double x = __ldcg(&ri[p]);
-        const double y = fma(-c1, x, row[p]);
-        row[p] = y;
-        s = fma(x, y, s);
+      for (int p0 = threadIdx.x; p0 < P; p0 += step) {
+        double x[kSweepBatch];
+#pragma unroll
+        for (int u = 0; u < kSweepBatch; ++u) {
+          const int p = p0 + u * blockDim.x;
+          x[u] = p < P ? __ldcg(&ri[p]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kSweepBatch; ++u) {
+          const int p = p0 + u * blockDim.x;
+          if (p < P) {
+            const double y = fma(-c1, x[u], row[p]);
+            row[p] = y;
+            s = fma(x[u], y, s);
+          }
+        }
       }
       const double c2 = block_sum(s, red) * inv * inv;
       s = 0.0;
-      for (int p = threadIdx.x; p < P; p += blockDim.x) {
-        const double x = __ldcg(&ri[p]);
-        const double y = fma(-c2, x, row[p]);
-        row[p] = y;
-        __stcg(&rj[p], y);
-        s = fma(y, y, s);
+      for (int p0 = threadIdx.x; p0 < P; p0 += step) {
+        double x[kSweepBatch];
+#pragma unroll
+        for (int u = 0; u < kSweepBatch; ++u) {
+          const int p = p0 + u * blockDim.x;
+          x[u] = p < P ? __ldcg(&ri[p]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kSweepBatch; ++u) {
+          const int p = p0 + u * blockDim.x;
+          if (p < P) {
+            const double y = fma(-c2, x[u], row[p]);
+            row[p] = y;
+            __stcg(&rj[p], y);
+            s = fma(y, y, s);
+          }
+        }
       }
       s = block_sum(s, red);
       if (threadIdx.x == 0) __stcg(&rn2[j], s);
