@@ -285,6 +285,7 @@ class Closure {
   // rows and transposed rows with a fixed exponent (|v| <= 1), flagged rows
   // and their coefficients in chunks of kOzRows with per-row exponents
   static constexpr int kOzRows = 2048;
+  static constexpr int kOzMinK = 64;   // contractions shorter than one k-box run on zero-padded slices
   static constexpr size_t kOzWs = size_t(8) << 20;   // split-K partials, doubles (64 MB)
   bool oz_on_ = false;
   int oz_beta_ = 0, oz_S_ = 0, oz_rows_ = 0;
@@ -446,6 +447,8 @@ class Closure {
       LC_TRY(cudaMemsetAsync(Blo_, 0, sizeof(__nv_bfloat16) * (size_t)Kpad_ * ncap_pad_, s_));
       LC_TRY(cudaMemsetAsync(Chi_, 0, sizeof(__nv_bfloat16) * (size_t)Kpad_ * ldp_, s_));
       LC_TRY(cudaMemsetAsync(Clo_, 0, sizeof(__nv_bfloat16) * (size_t)Kpad_ * ldp_, s_));
+      // columns of V's transposed slices past the rows sliced so far stay zero digits
+      if (oz_on_) LC_TRY(cudaMemsetAsync(VsT_, 0, sizeof(__nv_bfloat16) * (size_t)oz_S_ * ldp_ * ncap_pad_, s_));
     }
     if (ldp_ > P_) {
       // padding columns of the FP64 rows stay zero
@@ -563,8 +566,8 @@ class Closure {
     return e;
   }
   // the tensor-core form where the FP64 product is long enough to pay for
-  // the slicing (about 2^30 multiply-adds and up)
-  bool oz_use(int f, int n0) const { return oz_on_ && n0 >= 64 && (double)f * n0 * P_ >= 1073741824.0; }
+  // the slicing (about 2^27 multiply-adds and up)
+  bool oz_use(int f, int n0) const { return oz_on_ && n0 >= 1 && (double)f * n0 * P_ >= 134217728.0; }
 
   // W^T slices of V rows [w0, w0 + nw) (nw <= kPanel) for the panel projections
   cudaError_t oz_sync_w(int w0, int nw) {
@@ -572,6 +575,10 @@ class Closure {
     oz_w0_ = w0;
     oz_nw_ = nw;
     launches_ += 1;
+    if (nw < kOzMinK) {   // the columns a short contraction pads to must be zero digits
+      const cudaError_t e = cudaMemsetAsync(WsT_, 0, sizeof(__nv_bfloat16) * (size_t)oz_S_ * ldp_ * kPanel, s_);
+      if (e != cudaSuccess) return e;
+    }
     return oz_slice_cols(V64_, w0, w0 + nw, P_, ldp_, oz_S_, oz_beta_, 1, WsT_, ldp_, kPanel, s_, w0);
   }
 
@@ -608,14 +615,15 @@ class Closure {
     cudaError_t e = w0 == 0 ? oz_sync_v(nw) : oz_sync_w(w0, nw);
     for (int r0 = 0; r0 < f && e == cudaSuccess; r0 += kOzRows) {
       const int c = std::min(kOzRows, f - r0);
+      const int kg = std::max(nw, kOzMinK);   // zero digits beyond nw on both sides
       e = oz_slice_rows(beta64_ + (size_t)r0 * ncap_, c, nw, (int)ncap_, oz_S_, oz_beta_, 0, Cs_, kOzRows,
-                        ncap_pad_, eC_, 0, run_if, s_);
+                        ncap_pad_, eC_, 0, run_if, s_, kg);
       launches_ += 1;
       if (e != cudaSuccess) break;
       const OzOperand A{Cs_, kOzRows, ncap_pad_, eC_, 0};
       const OzOperand B = w0 == 0 ? OzOperand{VsT_, ldp_, ncap_pad_, nullptr, 1}
                                   : OzOperand{WsT_, ldp_, kPanel, nullptr, 1};
-      e = ozaki_gemm_nt(c, P_, nw, A, B, oz_S_, oz_beta_, Rb + (size_t)r0 * ldp_, ldp_, true, oz_ws_, kOzWs, run_if,
+      e = ozaki_gemm_nt(c, P_, kg, A, B, oz_S_, oz_beta_, Rb + (size_t)r0 * ldp_, ldp_, true, oz_ws_, kOzWs, run_if,
                         opt.spin_cap, st_, s_, &launches_);
       oz_gemms_ += 1;
     }

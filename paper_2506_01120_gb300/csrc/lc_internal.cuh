@@ -219,10 +219,11 @@ int oz_beta_for(int K);          // digit width for contractions up to K terms
 int oz_slices_for(int beta);     // slices for >= 54 bits
 long long oz_max_k(int beta);    // longest exact FP32 chain for that width
 // rows [0, rows) of X into slice rows [row0, row0 + rows); per-row exponents
-// to exps[row0 + r] (or fixed_e when exps is null)
+// to exps[row0 + r] (or fixed_e when exps is null); columns [cols, cols_pad)
+// of the slices are written as zero digits
 cudaError_t oz_slice_rows(const double* X, int rows, int cols, int ldx, int S, int beta, int fixed_e,
                           __nv_bfloat16* out, int rows_alloc, int lds, int* exps, int row0, const int* run_if,
-                          cudaStream_t s);
+                          cudaStream_t s, int cols_pad = 0);
 // rows [r0, r1) of V as columns j - jbase of the transposed slices
 // outT[s][p][j - jbase] (fixed exponent)
 cudaError_t oz_slice_cols(const double* V, int r0, int r1, int P, int ldv, int S, int beta, int e,

@@ -1730,8 +1730,8 @@ __device__ __forceinline__ int oz_row_exp(long long maxbits) {
 
 // One warp per row of X (FP64): per-row exponent (or the fixed one when
 // exps is null), then the digits into slices[s][row0 + r][c].
-__global__ void k_oz_slice_rows(const double* __restrict__ X, int rows, int cols, int ldx, int S, int beta,
-                                int fixed_e, __nv_bfloat16* __restrict__ out, int rows_alloc, int lds,
+__global__ void k_oz_slice_rows(const double* __restrict__ X, int rows, int cols, int cols_pad, int ldx, int S,
+                                int beta, int fixed_e, __nv_bfloat16* __restrict__ out, int rows_alloc, int lds,
                                 int* __restrict__ exps, int row0, const int* __restrict__ run_if) {
   if (run_if && *run_if == 0) return;
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -1749,6 +1749,8 @@ __global__ void k_oz_slice_rows(const double* __restrict__ X, int rows, int cols
   const long long sstride = (long long)rows_alloc * lds;
   __nv_bfloat16* o = out + (long long)(row0 + r) * lds;
   for (int c = lane; c < cols; c += 32) oz_digits(x[c], e, S, beta, o + c, sstride);
+  for (int c = cols + lane; c < cols_pad; c += 32)   // zero digits up to the k-box width
+    for (int s = 0; s < S; ++s) o[s * sstride + c] = __float2bfloat16_rn(0.f);
 }
 
 // Rows [r0, r1) of V (FP64) as columns j - jbase of the transposed slices
@@ -1785,11 +1787,12 @@ long long oz_max_k(int beta) { return 1LL << (26 - 2 * beta); }
 
 cudaError_t oz_slice_rows(const double* X, int rows, int cols, int ldx, int S, int beta, int fixed_e,
                           __nv_bfloat16* out, int rows_alloc, int lds, int* exps, int row0, const int* run_if,
-                          cudaStream_t s) {
+                          cudaStream_t s, int cols_pad) {
   if (rows <= 0 || cols <= 0) return cudaSuccess;
-  if (row0 < 0 || row0 + rows > rows_alloc || cols > lds || beta < 1 || beta > 7) return cudaErrorInvalidValue;
-  k_oz_slice_rows<<<(rows + 7) / 8, 256, 0, s>>>(X, rows, cols, ldx, S, beta, fixed_e, out, rows_alloc, lds, exps,
-                                                 row0, run_if);
+  cols_pad = std::max(cols, cols_pad);
+  if (row0 < 0 || row0 + rows > rows_alloc || cols_pad > lds || beta < 1 || beta > 7) return cudaErrorInvalidValue;
+  k_oz_slice_rows<<<(rows + 7) / 8, 256, 0, s>>>(X, rows, cols, cols_pad, ldx, S, beta, fixed_e, out, rows_alloc,
+                                                 lds, exps, row0, run_if);
   return cudaGetLastError();
 }
 
