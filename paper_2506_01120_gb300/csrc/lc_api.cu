@@ -282,15 +282,17 @@ class Closure {
   float* rho2f_ = nullptr;            // screened rho^2 of the flagged candidates, flag order
   int* cidx_ = nullptr;               // compacted (GEMM-row) positions of the flagged candidates
   // FP64-accurate tensor-core GEMMs of the accept step (digit slices): V's
-  // rows and transposed rows with a fixed exponent (|v| <= 1), flagged rows
-  // and their coefficients in chunks of kOzRows with per-row exponents
+  // rows and transposed rows, each row in units of its own exponent eV (the
+  // coefficients of R -= c V carry 2^eV in their columns), flagged rows and
+  // their coefficients in chunks of kOzRows with per-row exponents; slice
+  // pairs up to level S (one past the slices' own resolution)
   static constexpr int kOzRows = 2048;
   static constexpr int kOzMinK = 64;   // contractions shorter than one k-box run on zero-padded slices
   static constexpr size_t kOzWs = size_t(8) << 20;   // split-K partials, doubles (64 MB)
   bool oz_on_ = false;
   int oz_beta_ = 0, oz_S_ = 0, oz_rows_ = 0;
   __nv_bfloat16 *Vs_ = nullptr, *VsT_ = nullptr, *Rs_ = nullptr, *Cs_ = nullptr;
-  int *eR_ = nullptr, *eC_ = nullptr;
+  int *eR_ = nullptr, *eC_ = nullptr, *eV_ = nullptr;   // row exponents (eV_: V's rows)
   __nv_bfloat16* WsT_ = nullptr;      // transposed slices of one panel's accepted rows
   int oz_w0_ = -1, oz_nw_ = -1;
   double* oz_ws_ = nullptr;
@@ -399,6 +401,7 @@ class Closure {
         Cs_ = ar_.take<__nv_bfloat16>((size_t)oz_S_ * kOzRows * ncap_pad_);
         WsT_ = ar_.take<__nv_bfloat16>((size_t)oz_S_ * ldp_ * kPanel);
         eR_ = ar_.take<int>(kOzRows);
+        eV_ = ar_.take<int>(ncap_pad_);
         eC_ = ar_.take<int>(kOzRows);
         oz_ws_ = ar_.take<double>(kOzWs);
       }
@@ -557,10 +560,10 @@ class Closure {
   // V rows [oz_rows_, n0) into both slice layouts (rows are final once appended)
   cudaError_t oz_sync_v(int n0) {
     if (n0 <= oz_rows_) return cudaSuccess;
-    cudaError_t e = oz_slice_rows(V64_ + (size_t)oz_rows_ * ldp_, n0 - oz_rows_, P_, ldp_, oz_S_, oz_beta_, 1, Vs_,
-                                  ncap_pad_, ldp_, nullptr, oz_rows_, nullptr, s_);
+    cudaError_t e = oz_slice_rows(V64_ + (size_t)oz_rows_ * ldp_, n0 - oz_rows_, P_, ldp_, oz_S_, oz_beta_, 0, Vs_,
+                                  ncap_pad_, ldp_, eV_, oz_rows_, nullptr, s_);
     if (e == cudaSuccess)
-      e = oz_slice_cols(V64_, oz_rows_, n0, P_, ldp_, oz_S_, oz_beta_, 1, VsT_, ldp_, ncap_pad_, s_);
+      e = oz_slice_cols(V64_, oz_rows_, n0, P_, ldp_, oz_S_, oz_beta_, eV_, VsT_, ldp_, ncap_pad_, s_);
     launches_ += 2;
     oz_rows_ = n0;
     return e;
@@ -579,7 +582,7 @@ class Closure {
       const cudaError_t e = cudaMemsetAsync(WsT_, 0, sizeof(__nv_bfloat16) * (size_t)oz_S_ * ldp_ * kPanel, s_);
       if (e != cudaSuccess) return e;
     }
-    return oz_slice_cols(V64_, w0, w0 + nw, P_, ldp_, oz_S_, oz_beta_, 1, WsT_, ldp_, kPanel, s_, w0);
+    return oz_slice_cols(V64_, w0, w0 + nw, P_, ldp_, oz_S_, oz_beta_, eV_, WsT_, ldp_, kPanel, s_, w0);
   }
 
   // beta64 rows [0, f) (row stride ncap) = rows [0, f) of R (from Rb) times
@@ -598,9 +601,9 @@ class Closure {
                         s_);
       launches_ += 1;
       if (e != cudaSuccess) break;
-      const OzOperand A{Rs_, kOzRows, ldp_, eR_, 0}, B{Vs_ + (size_t)w0 * ldp_, ncap_pad_, ldp_, nullptr, 1, vtot};
+      const OzOperand A{Rs_, kOzRows, ldp_, eR_, 0}, B{Vs_ + (size_t)w0 * ldp_, ncap_pad_, ldp_, eV_ + w0, 0, vtot};
       e = ozaki_gemm_nt(c, nw, P_, A, B, oz_S_, oz_beta_, beta64_ + (size_t)r0 * ncap_, (int)ncap_, false, oz_ws_,
-                        kOzWs, run_if, opt.spin_cap, st_, s_, &launches_);
+                        kOzWs, run_if, opt.spin_cap, st_, s_, &launches_, oz_S_);
       oz_gemms_ += 1;
     }
     return e;
@@ -616,15 +619,17 @@ class Closure {
     for (int r0 = 0; r0 < f && e == cudaSuccess; r0 += kOzRows) {
       const int c = std::min(kOzRows, f - r0);
       const int kg = std::max(nw, kOzMinK);   // zero digits beyond nw on both sides
+      // coefficient column j carries V row (w0 + j)'s scale 2^eV, the
+      // transposed slices hold V in units of it
       e = oz_slice_rows(beta64_ + (size_t)r0 * ncap_, c, nw, (int)ncap_, oz_S_, oz_beta_, 0, Cs_, kOzRows,
-                        ncap_pad_, eC_, 0, run_if, s_, kg);
+                        ncap_pad_, eC_, 0, run_if, s_, kg, eV_ + w0);
       launches_ += 1;
       if (e != cudaSuccess) break;
       const OzOperand A{Cs_, kOzRows, ncap_pad_, eC_, 0};
-      const OzOperand B = w0 == 0 ? OzOperand{VsT_, ldp_, ncap_pad_, nullptr, 1}
-                                  : OzOperand{WsT_, ldp_, kPanel, nullptr, 1};
+      const OzOperand B = w0 == 0 ? OzOperand{VsT_, ldp_, ncap_pad_, nullptr, 0}
+                                  : OzOperand{WsT_, ldp_, kPanel, nullptr, 0};
       e = ozaki_gemm_nt(c, P_, kg, A, B, oz_S_, oz_beta_, Rb + (size_t)r0 * ldp_, ldp_, true, oz_ws_, kOzWs, run_if,
-                        opt.spin_cap, st_, s_, &launches_);
+                        opt.spin_cap, st_, s_, &launches_, oz_S_);
       oz_gemms_ += 1;
     }
     return e;

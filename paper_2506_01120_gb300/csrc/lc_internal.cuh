@@ -221,18 +221,23 @@ long long oz_max_k(int beta);    // longest exact FP32 chain for that width
 // rows [0, rows) of X into slice rows [row0, row0 + rows); per-row exponents
 // to exps[row0 + r] (or fixed_e when exps is null); columns [cols, cols_pad)
 // of the slices are written as zero digits
+// (col_exp: column c sliced as x[c] 2^col_exp[c])
 cudaError_t oz_slice_rows(const double* X, int rows, int cols, int ldx, int S, int beta, int fixed_e,
                           __nv_bfloat16* out, int rows_alloc, int lds, int* exps, int row0, const int* run_if,
-                          cudaStream_t s, int cols_pad = 0);
+                          cudaStream_t s, int cols_pad = 0, const int* col_exp = nullptr);
 // rows [r0, r1) of V as columns j - jbase of the transposed slices
-// outT[s][p][j - jbase] (fixed exponent)
-cudaError_t oz_slice_cols(const double* V, int r0, int r1, int P, int ldv, int S, int beta, int e,
+// outT[s][p][j - jbase], row j in units of 2^row_exp[j]
+cudaError_t oz_slice_cols(const double* V, int r0, int r1, int P, int ldv, int S, int beta, const int* row_exp,
                           __nv_bfloat16* outT, int P_alloc, int ldt, cudaStream_t s, int jbase = 0);
 // C (M x N, ldc) = A B^T (or C -= A B^T) to FP64 accuracy; ws holds the
 // FP64 partials of a K split (M * N doubles per split)
+// max_level: slice pairs (s, t) with s + t <= max_level run (default S - 1;
+// S keeps one level more, which brings the pairs dropped below the slices'
+// own rounding)
 cudaError_t ozaki_gemm_nt(int M, int N, int K, const OzOperand& A, const OzOperand& B, int S, int beta, double* C,
                           int ldc, bool subtract, double* ws, size_t ws_doubles, const int* run_if,
-                          long long spin_cap, DevStatus* st, cudaStream_t s, long long* launches);
+                          long long spin_cap, DevStatus* st, cudaStream_t s, long long* launches,
+                          int max_level = -1);
 
 // ------------------------------------------------------ mixed-precision path
 // (lc_mixed.cu)

@@ -1732,31 +1732,37 @@ __device__ __forceinline__ int oz_row_exp(long long maxbits) {
 // exps is null), then the digits into slices[s][row0 + r][c].
 __global__ void k_oz_slice_rows(const double* __restrict__ X, int rows, int cols, int cols_pad, int ldx, int S,
                                 int beta, int fixed_e, __nv_bfloat16* __restrict__ out, int rows_alloc, int lds,
-                                int* __restrict__ exps, int row0, const int* __restrict__ run_if) {
+                                int* __restrict__ exps, int row0, const int* __restrict__ col_exp,
+                                const int* __restrict__ run_if) {
   if (run_if && *run_if == 0) return;
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (r >= rows) return;
   const double* x = X + (long long)r * ldx;
+  // column c of the row is sliced as x[c] 2^col_exp[c] when col_exp is given
+  auto val = [&](int c) { return col_exp ? scalbn(x[c], col_exp[c]) : x[c]; };
   int e = fixed_e;
   if (exps) {
     long long m = 0;
-    for (int c = lane; c < cols; c += 32) m = max(m, __double_as_longlong(x[c]) & 0x7FFFFFFFFFFFFFFFLL);
+    for (int c = lane; c < cols; c += 32) m = max(m, __double_as_longlong(val(c)) & 0x7FFFFFFFFFFFFFFFLL);
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     e = oz_row_exp(m);
     if (lane == 0) exps[row0 + r] = e;
   }
   const long long sstride = (long long)rows_alloc * lds;
   __nv_bfloat16* o = out + (long long)(row0 + r) * lds;
-  for (int c = lane; c < cols; c += 32) oz_digits(x[c], e, S, beta, o + c, sstride);
+  for (int c = lane; c < cols; c += 32) oz_digits(val(c), e, S, beta, o + c, sstride);
   for (int c = cols + lane; c < cols_pad; c += 32)   // zero digits up to the k-box width
     for (int s = 0; s < S; ++s) o[s * sstride + c] = __float2bfloat16_rn(0.f);
 }
 
 // Rows [r0, r1) of V (FP64) as columns j - jbase of the transposed slices
-// outT[s][p][j - jbase] (fixed exponent), through a 32 x 32 shared-memory tile.
+// outT[s][p][j - jbase], row j in units of its own exponent row_exp[j] (the
+// product's other operand carries 2^row_exp[j] in its column j), through a
+// 32 x 32 shared-memory tile.
 __global__ void k_oz_slice_cols(const double* __restrict__ V, int r0, int r1, int P, int ldv, int S, int beta,
-                                int e, __nv_bfloat16* __restrict__ outT, int P_alloc, int ldt, int jbase) {
+                                const int* __restrict__ row_exp, __nv_bfloat16* __restrict__ outT, int P_alloc,
+                                int ldt, int jbase) {
   __shared__ double tile[32][33];
   const int j0 = r0 + blockIdx.y * 32, p0 = blockIdx.x * 32;
   for (int k = threadIdx.y; k < 32; k += blockDim.y) {
@@ -1767,7 +1773,8 @@ __global__ void k_oz_slice_cols(const double* __restrict__ V, int r0, int r1, in
   const long long sstride = (long long)P_alloc * ldt;
   for (int k = threadIdx.y; k < 32; k += blockDim.y) {
     const int pp = p0 + k, j = j0 + threadIdx.x;
-    if (pp < P && j < r1) oz_digits(tile[threadIdx.x][k], e, S, beta, outT + (long long)pp * ldt + (j - jbase), sstride);
+    if (pp < P && j < r1)
+      oz_digits(tile[threadIdx.x][k], row_exp[j], S, beta, outT + (long long)pp * ldt + (j - jbase), sstride);
   }
 }
 
@@ -1787,28 +1794,28 @@ long long oz_max_k(int beta) { return 1LL << (26 - 2 * beta); }
 
 cudaError_t oz_slice_rows(const double* X, int rows, int cols, int ldx, int S, int beta, int fixed_e,
                           __nv_bfloat16* out, int rows_alloc, int lds, int* exps, int row0, const int* run_if,
-                          cudaStream_t s, int cols_pad) {
+                          cudaStream_t s, int cols_pad, const int* col_exp) {
   if (rows <= 0 || cols <= 0) return cudaSuccess;
   cols_pad = std::max(cols, cols_pad);
   if (row0 < 0 || row0 + rows > rows_alloc || cols_pad > lds || beta < 1 || beta > 7) return cudaErrorInvalidValue;
   k_oz_slice_rows<<<(rows + 7) / 8, 256, 0, s>>>(X, rows, cols, cols_pad, ldx, S, beta, fixed_e, out, rows_alloc,
-                                                 lds, exps, row0, run_if);
+                                                 lds, exps, row0, col_exp, run_if);
   return cudaGetLastError();
 }
 
-cudaError_t oz_slice_cols(const double* V, int r0, int r1, int P, int ldv, int S, int beta, int e,
+cudaError_t oz_slice_cols(const double* V, int r0, int r1, int P, int ldv, int S, int beta, const int* row_exp,
                           __nv_bfloat16* outT, int P_alloc, int ldt, cudaStream_t s, int jbase) {
   if (r1 <= r0 || P <= 0) return cudaSuccess;
   if (P > P_alloc || jbase < 0 || jbase > r0 || r1 - jbase > ldt || beta < 1 || beta > 7)
     return cudaErrorInvalidValue;
   dim3 grid((unsigned)((P + 31) / 32), (unsigned)((r1 - r0 + 31) / 32));
-  k_oz_slice_cols<<<grid, dim3(32, 8), 0, s>>>(V, r0, r1, P, ldv, S, beta, e, outT, P_alloc, ldt, jbase);
+  k_oz_slice_cols<<<grid, dim3(32, 8), 0, s>>>(V, r0, r1, P, ldv, S, beta, row_exp, outT, P_alloc, ldt, jbase);
   return cudaGetLastError();
 }
 
 cudaError_t ozaki_gemm_nt(int M, int N, int K, const OzOperand& A, const OzOperand& B, int S, int beta, double* C,
                           int ldc, bool subtract, double* ws, size_t ws_doubles, const int* run_if,
-                          long long spin_cap, DevStatus* st, cudaStream_t s, long long* launches) {
+                          long long spin_cap, DevStatus* st, cudaStream_t s, long long* launches, int max_level) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   if (beta < 1 || beta > 7 || S < 1 || (A.ld % 8) || (B.ld % 8) || K > A.ld || K > B.ld || M > A.rows ||
       N > B.rows)
@@ -1861,15 +1868,18 @@ cudaError_t ozaki_gemm_nt(int M, int N, int K, const OzOperand& A, const OzOpera
   // chains: up to g pairs of a level share an accumulator while
   // g (kchunk OZ_BK) 2^(2 beta - 2) <= 2^24
   const int g = (int)std::max<long long>(1, oz_max_k(beta) / ((long long)kchunk * OZ_BK));
+  const int L = max_level >= 0 ? std::min(max_level, 2 * S - 2) : S - 1;
   p.nchains = 0;
-  for (int l = 0; l < S; ++l)
-    for (int s0 = 0; s0 <= l; s0 += g) {
+  for (int l = 0; l <= L; ++l) {
+    const int s_lo = std::max(0, l - (S - 1)), s_hi = std::min(l, S - 1);
+    for (int s0 = s_lo; s0 <= s_hi; s0 += g) {
       if (p.nchains >= 64) return cudaErrorInvalidValue;
       p.ch_level[p.nchains] = (signed char)l;
       p.ch_s0[p.nchains] = (signed char)s0;
-      p.ch_cnt[p.nchains] = (signed char)std::min(g, l + 1 - s0);
+      p.ch_cnt[p.nchains] = (signed char)std::min(g, s_hi + 1 - s0);
       ++p.nchains;
     }
+  }
   k_ozaki_gemm<<<(unsigned)(tiles * nsplit), OZ_THREADS, OZ_SMEM, s>>>(mA, mB, p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -1927,7 +1937,7 @@ extern "C" LC_API int lc_gemm_f64_tc(const double* A, const double* B, int M, in
     rc = LC_ERR_CUDA;
   if (rc == LC_OK) {
     const OzOperand oa{As, M, ld, eA, 0}, ob{Bs, N, ld, eB, 0};
-    if (ozaki_gemm_nt(M, N, ld, oa, ob, S, beta, C, N, false, ws, ws_doubles, nullptr, 0, st, s, nullptr) !=
+    if (ozaki_gemm_nt(M, N, ld, oa, ob, S, beta, C, N, false, ws, ws_doubles, nullptr, 0, st, s, nullptr, S) !=
         cudaSuccess)
       rc = LC_ERR_CUDA;
   }
