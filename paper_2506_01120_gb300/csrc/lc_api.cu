@@ -1247,7 +1247,10 @@ const char* lc_status_string(int s) {
   }
 }
 
-const char* lc_version(void) { return "lieclosure-gb300 0.4 (sm_103a; screening GEMM 128x256x32, split-K; d = 64 bracket M = 128 persistent)"; }
+const char* lc_version(void) {
+  return "lieclosure-gb300 0.5 (sm_103a; screening GEMM 128x256x32, split-K; d = 64 bracket M = 128 persistent; "
+         "FP64-accurate tensor-core accept projections; shared-memory in-block accept)";
+}
 
 int lie_closure_dev(const lc_c128* generators, int k, int d, double tol, lc_c128* basis_out, long long* dim_out,
                     long long max_dim, const lc_options* opt, lc_report* rep, void* stream) {
