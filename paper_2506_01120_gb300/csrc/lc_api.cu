@@ -569,8 +569,8 @@ class Closure {
     return e;
   }
   // the tensor-core form where the FP64 product is long enough to pay for
-  // the slicing (about 2^27 multiply-adds and up)
-  bool oz_use(int f, int n0) const { return oz_on_ && n0 >= 1 && (double)f * n0 * P_ >= 134217728.0; }
+  // the slicing and the launches (about 2^24 multiply-adds and up)
+  bool oz_use(int f, int n0) const { return oz_on_ && n0 >= 1 && (double)f * n0 * P_ >= 16777216.0; }
 
   // W^T slices of V rows [w0, w0 + nw) (nw <= kPanel) for the panel projections
   cudaError_t oz_sync_w(int w0, int nw) {

@@ -806,8 +806,10 @@ __global__ void __launch_bounds__(256) k_accept_wide(int f, double* __restrict__
 // pivot is read from global memory).  Per component and per partial sum
 // this is k_accept_seq's arithmetic in k_accept_seq's order; one bounded
 // grid barrier per accept.  The pivot's owner appends it to V.
-constexpr int kSweepBatch = 8;
-
+// NPT: components per thread (P <= 256 NPT); the pivot row is loaded into
+// registers once per accept (one round trip to L2 for all three sweeps), in
+// the same per-thread order of p as a strided loop.
+template <int NPT>
 __global__ void __launch_bounds__(256, 1) k_accept_rowsmem(int f, double* __restrict__ R, int ldr,
                                                            double* __restrict__ rn2, const double* __restrict__ hn2,
                                                            double tol_rel2, double tol_abs2, double eta2,
@@ -862,61 +864,40 @@ __global__ void __launch_bounds__(256, 1) k_accept_rowsmem(int f, double* __rest
         if (Bk) bn2[slot] = h2;
       }
     } else if (j > i) {
-      // each sweep loads the pivot in batches of kSweepBatch per thread
-      // ahead of the arithmetic (same per-thread order of p as a strided loop)
       const double* ri = R + (long long)i * ldr;
-      const int step = kSweepBatch * blockDim.x;
+      double x[NPT];
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) {
+        const int p = threadIdx.x + k * 256;
+        x[k] = p < P ? __ldcg(&ri[p]) : 0.0;
+      }
       double s = 0.0;
-      for (int p0 = threadIdx.x; p0 < P; p0 += step) {
-        double x[kSweepBatch];
 #pragma unroll
-        for (int u = 0; u < kSweepBatch; ++u) {
-          const int p = p0 + u * blockDim.x;
-          x[u] = p < P ? __ldcg(&ri[p]) : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < kSweepBatch; ++u) {
-          const int p = p0 + u * blockDim.x;
-          if (p < P) s = fma(x[u], row[p], s);
-        }
+      for (int k = 0; k < NPT; ++k) {
+        const int p = threadIdx.x + k * 256;
+        if (p < P) s = fma(x[k], row[p], s);
       }
       const double c1 = block_sum(s, red) * inv * inv;   // as k_accept_seq associates it
       s = 0.0;
-      for (int p0 = threadIdx.x; p0 < P; p0 += step) {
-        double x[kSweepBatch];
 #pragma unroll
-        for (int u = 0; u < kSweepBatch; ++u) {
-          const int p = p0 + u * blockDim.x;
-          x[u] = p < P ? __ldcg(&ri[p]) : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < kSweepBatch; ++u) {
-          const int p = p0 + u * blockDim.x;
-          if (p < P) {
-            const double y = fma(-c1, x[u], row[p]);
-            row[p] = y;
-            s = fma(x[u], y, s);
-          }
+      for (int k = 0; k < NPT; ++k) {
+        const int p = threadIdx.x + k * 256;
+        if (p < P) {
+          const double y = fma(-c1, x[k], row[p]);
+          row[p] = y;
+          s = fma(x[k], y, s);
         }
       }
       const double c2 = block_sum(s, red) * inv * inv;
       s = 0.0;
-      for (int p0 = threadIdx.x; p0 < P; p0 += step) {
-        double x[kSweepBatch];
 #pragma unroll
-        for (int u = 0; u < kSweepBatch; ++u) {
-          const int p = p0 + u * blockDim.x;
-          x[u] = p < P ? __ldcg(&ri[p]) : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < kSweepBatch; ++u) {
-          const int p = p0 + u * blockDim.x;
-          if (p < P) {
-            const double y = fma(-c2, x[u], row[p]);
-            row[p] = y;
-            __stcg(&rj[p], y);
-            s = fma(y, y, s);
-          }
+      for (int k = 0; k < NPT; ++k) {
+        const int p = threadIdx.x + k * 256;
+        if (p < P) {
+          const double y = fma(-c2, x[k], row[p]);
+          row[p] = y;
+          __stcg(&rj[p], y);
+          s = fma(y, y, s);
         }
       }
       s = block_sum(s, red);
@@ -1229,12 +1210,21 @@ size_t accept_wide_part_doubles() { return (size_t)3 * kAcceptWideMaxRows * (siz
 // 3 ceil((f - i - 1) / 8) CTA reductions per accept, which pay off once the
 // rows are long.
 // rows held in shared memory: one CTA per flagged row, all co-resident
+static const void* accept_rowsmem_kernel(int P) {
+  if (P <= 256) return (const void*)k_accept_rowsmem<1>;
+  if (P <= 1024) return (const void*)k_accept_rowsmem<4>;
+  if (P <= 4096) return (const void*)k_accept_rowsmem<16>;
+  if (P <= 16384) return (const void*)k_accept_rowsmem<64>;
+  return nullptr;
+}
+
 static bool accept_rowsmem_fits(int f, int P) {
-  if ((size_t)P * sizeof(double) > kAcceptRowSmemMax) return false;
+  const void* kern = accept_rowsmem_kernel(P);
+  if (!kern || (size_t)P * sizeof(double) > kAcceptRowSmemMax) return false;
   const int bytes = P * (int)sizeof(double);
-  if (smem_optin((const void*)k_accept_rowsmem, bytes) != cudaSuccess) return false;
+  if (smem_optin(kern, bytes) != cudaSuccess) return false;
   int per = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_accept_rowsmem, 256, bytes) != cudaSuccess) return false;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, bytes) != cudaSuccess) return false;
   return f <= per * device_sm_count();
 }
 
@@ -1267,7 +1257,7 @@ cudaError_t accept_seq(int f, double* R, int ldr, double* rn2, const double* hn2
     void* args[] = {&f,     &R,   &ldr, &rn2, (void*)&hn2, &tol_rel2,    &tol_abs2, &eta2, &V,   &ldv,
                     &ncap,  &P,   &stats, &st, &bar,       &lim,         &phantom,  (void*)&Hraw, &Bk, &bn2,
                     (void*)&rho2_screen};
-    return cudaLaunchCooperativeKernel((const void*)k_accept_rowsmem, dim3(f), dim3(256), args,
+    return cudaLaunchCooperativeKernel(accept_rowsmem_kernel(P), dim3(f), dim3(256), args,
                                        (size_t)P * sizeof(double), s);
   }
   const int nblocks = coresident_ctas((const void*)k_accept_seq, 0);

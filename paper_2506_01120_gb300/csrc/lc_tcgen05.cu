@@ -1728,32 +1728,54 @@ __device__ __forceinline__ int oz_row_exp(long long maxbits) {
   return ex == 0 ? 0 : ex - 1023 + 2;
 }
 
-// One warp per row of X (FP64): per-row exponent (or the fixed one when
-// exps is null), then the digits into slices[s][row0 + r][c].
-__global__ void k_oz_slice_rows(const double* __restrict__ X, int rows, int cols, int cols_pad, int ldx, int S,
-                                int beta, int fixed_e, __nv_bfloat16* __restrict__ out, int rows_alloc, int lds,
-                                int* __restrict__ exps, int row0, const int* __restrict__ col_exp,
-                                const int* __restrict__ run_if) {
+// Digits of two neighbouring entries, stored as BF16 pairs (one 4-byte store
+// per slice for both).
+__device__ __forceinline__ void oz_digits2(double x0, double x1, int e, int S, int beta, __nv_bfloat162* out,
+                                           long long sstride2) {
+  long long Y0 = oz_fixed(x0, beta * S - e), Y1 = oz_fixed(x1, beta * S - e);
+  const long long half = 1LL << (beta - 1), mask = (1LL << beta) - 1;
+  for (int s = S - 1; s >= 1; --s) {
+    const long long d0 = ((Y0 + half) & mask) - half, d1 = ((Y1 + half) & mask) - half;
+    Y0 = (Y0 - d0) >> beta;
+    Y1 = (Y1 - d1) >> beta;
+    out[s * sstride2] = __floats2bfloat162_rn((float)d0, (float)d1);
+  }
+  out[0] = __floats2bfloat162_rn((float)Y0, (float)Y1);
+}
+
+// One CTA of kOzSliceThreads per row of X (FP64): per-row exponent (or the
+// fixed one when exps is null), then the digits into slices[s][row0 + r][c],
+// two columns per thread (lds even); columns [cols, cols_pad) get zero digits.
+constexpr int kOzSliceThreads = 128;
+
+__global__ void __launch_bounds__(kOzSliceThreads)
+    k_oz_slice_rows(const double* __restrict__ X, int rows, int cols, int cols_pad, int ldx, int S, int beta,
+                    int fixed_e, __nv_bfloat16* __restrict__ out, int rows_alloc, int lds, int* __restrict__ exps,
+                    int row0, const int* __restrict__ col_exp, const int* __restrict__ run_if) {
   if (run_if && *run_if == 0) return;
-  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (r >= rows) return;
+  __shared__ long long wmax[kOzSliceThreads / 32];
+  const int r = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const double* x = X + (long long)r * ldx;
   // column c of the row is sliced as x[c] 2^col_exp[c] when col_exp is given
-  auto val = [&](int c) { return col_exp ? scalbn(x[c], col_exp[c]) : x[c]; };
+  auto val = [&](int c) { return c < cols ? (col_exp ? scalbn(x[c], col_exp[c]) : x[c]) : 0.0; };
   int e = fixed_e;
   if (exps) {
     long long m = 0;
-    for (int c = lane; c < cols; c += 32) m = max(m, __double_as_longlong(val(c)) & 0x7FFFFFFFFFFFFFFFLL);
+    for (int c = threadIdx.x; c < cols; c += blockDim.x)
+      m = max(m, __double_as_longlong(val(c)) & 0x7FFFFFFFFFFFFFFFLL);
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) wmax[w] = m;
+    __syncthreads();
+    m = wmax[0];
+    for (int i = 1; i < kOzSliceThreads / 32; ++i) m = max(m, wmax[i]);
     e = oz_row_exp(m);
-    if (lane == 0) exps[row0 + r] = e;
+    if (threadIdx.x == 0) exps[row0 + r] = e;
   }
-  const long long sstride = (long long)rows_alloc * lds;
-  __nv_bfloat16* o = out + (long long)(row0 + r) * lds;
-  for (int c = lane; c < cols; c += 32) oz_digits(val(c), e, S, beta, o + c, sstride);
-  for (int c = cols + lane; c < cols_pad; c += 32)   // zero digits up to the k-box width
-    for (int s = 0; s < S; ++s) o[s * sstride + c] = __float2bfloat16_rn(0.f);
+  const long long sstride2 = (long long)rows_alloc * lds / 2;
+  __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + (long long)(row0 + r) * lds);
+  const int ncol = max(cols, cols_pad);
+  for (int c = 2 * threadIdx.x; c < ncol; c += 2 * blockDim.x) oz_digits2(val(c), val(c + 1), e, S, beta, o + c / 2, sstride2);
 }
 
 // Rows [r0, r1) of V (FP64) as columns j - jbase of the transposed slices
@@ -1780,6 +1802,9 @@ __global__ void k_oz_slice_cols(const double* __restrict__ V, int r0, int r1, in
 
 }  // namespace
 
+// columns the row slicer writes (pairs): max(cols, cols_pad) rounded up to even
+static int ncol_even_check(int cols_pad, int cols) { return (std::max(cols, cols_pad) + 1) & ~1; }
+
 int oz_beta_for(int K) {
   // largest beta <= 7 with K 2^{2 beta - 2} <= 2^24
   int lg = 0;
@@ -1798,8 +1823,9 @@ cudaError_t oz_slice_rows(const double* X, int rows, int cols, int ldx, int S, i
   if (rows <= 0 || cols <= 0) return cudaSuccess;
   cols_pad = std::max(cols, cols_pad);
   if (row0 < 0 || row0 + rows > rows_alloc || cols_pad > lds || beta < 1 || beta > 7) return cudaErrorInvalidValue;
-  k_oz_slice_rows<<<(rows + 7) / 8, 256, 0, s>>>(X, rows, cols, cols_pad, ldx, S, beta, fixed_e, out, rows_alloc,
-                                                 lds, exps, row0, col_exp, run_if);
+  if ((lds & 1) || (ncol_even_check(cols_pad, cols) > lds)) return cudaErrorInvalidValue;
+  k_oz_slice_rows<<<rows, kOzSliceThreads, 0, s>>>(X, rows, cols, cols_pad, ldx, S, beta, fixed_e, out, rows_alloc,
+                                                   lds, exps, row0, col_exp, run_if);
   return cudaGetLastError();
 }
 
