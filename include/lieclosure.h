@@ -134,7 +134,7 @@ typedef struct {
                                  2 = every row sliced across all SMs (panels of
                                  at most 128 rows), 3 = one CTA per flagged
                                  row holding it in shared memory (rows of at
-                                 most 25,600 components; else 1).  All take
+                                 most 16,384 components; else 1).  All take
                                  the same decisions in the same order; 1 and 3
                                  compute identical values, 2 differs in the
                                  order of the FP64 partial sums */

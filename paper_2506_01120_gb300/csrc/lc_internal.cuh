@@ -165,7 +165,7 @@ cudaError_t rownorm2_f64(int M, int N, const double* A, int lda, double* out, cu
 // kernel: 1 = one CTA per row (k_accept_seq), 2 = every row sliced across the
 // grid (k_accept_wide; f <= kAcceptWideMaxRows, wpart holds
 // accept_wide_part_doubles() doubles), 3 = one CTA per row with the row in
-// shared memory (k_accept_rowsmem; P doubles <= kAcceptRowSmemMax bytes, f
+// shared memory (k_accept_rowsmem; P <= 16384 and P doubles <= kAcceptRowSmemMax bytes, f
 // co-resident CTAs), 0 = by shape
 constexpr int kAcceptWideMaxRows = 128;
 constexpr size_t kAcceptRowSmemMax = 200 * 1024;
